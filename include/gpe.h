@@ -1,0 +1,143 @@
+/*
+ * gpe.h -- C ABI of the GB300 spin-1 Gross-Pitaevskii split-step library (libgpe.so).
+ *
+ * Method: "Universal Dynamics at the Lowest Temperatures", Sec. 2.2.  The library
+ * propagates many truncated-Wigner trajectories of the three-component equation
+ * Eq. (GPE) on periodic 1D/2D/3D grids with the paper's split-step Fourier scheme
+ * (kinetic step in momentum space, diagonal phase step, off-diagonal 3x3 spin-mixing
+ * step with predictor), symmetrised as K(dt/2) D(dt/2) O(dt) D(dt/2) K(dt/2), and
+ * accumulates the ensemble spectra of Sec. 2.1 (occupations n_m(k), transverse spin
+ * structure factor S_perp(k)) plus norm / energy diagnostics in FP64.
+ *
+ * Conventions shared by every entry point:
+ *  - hbar = m = 1, no external potential.  Field components are ordered
+ *    (psi_1, psi_0, psi_-1).
+ *  - Field layout of one trajectory: [3][n2][n1][n0] complex numbers, contiguous,
+ *    x (n[0]) fastest; complex = interleaved (re, im) float (GPE_C64) or double
+ *    (GPE_C128).  The buffer must be 16-byte aligned.
+ *  - Memory: every buffer passed in is caller-owned device memory unless stated; the
+ *    library never frees caller memory.  The handle owns its tables and workspace.
+ *  - Streams: ``stream`` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued asynchronously; results are valid once the stream
+ *    has reached the point after the call.
+ *  - Errors: argument and CUDA launch errors are returned synchronously as a
+ *    gpe_status; gpe_last_error() gives a thread-local message.  Device-side
+ *    conditions (non-finite values, bounded waits that expired) latch in a status word
+ *    that gpe_sync_status() reads.  No C++ exception crosses the ABI.
+ */
+#ifndef GPE_H
+#define GPE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPE_OK = 0,
+    GPE_EINVAL = 1,        /* invalid argument (sizes, pointers, alignment, flags)      */
+    GPE_ENOMEM = 2,        /* device allocation for the handle's workspace failed       */
+    GPE_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed               */
+    GPE_ETIMEOUT = 4,      /* a bounded device-side wait expired                        */
+    GPE_ENONFINITE = 5,    /* a reduction met a non-finite value                        */
+    GPE_EUNSUPPORTED = 6   /* valid request that this build does not implement          */
+} gpe_status;
+
+typedef enum { GPE_C64 = 0, GPE_C128 = 1 } gpe_dtype;
+
+/* One trajectory.  ndim in {1,2,3}; n[a] = points along axis a (x = 0), each a power
+ * of two in [64, 1024] for ndim >= 2 and in [64, 8192] (C64) / [64, 4096] (C128) for
+ * ndim = 1; unused axes must be 1.  dx = lattice spacing (all axes).  psi = device
+ * pointer to the [3][n2][n1][n0] field (caller-owned, 16-byte aligned). */
+typedef struct {
+    int32_t ndim;
+    int32_t n[3];
+    double dx;
+    void* psi;
+} gpe_traj;
+
+/* Couplings of Eq. (GPE) and the time step.  q is constant when n_knots == 0;
+ * otherwise q(t) is piecewise linear through q_knots[j] at t_j = j t_end / (n_knots-1),
+ * clamped outside [0, t_end], and step n (time t_n = n dt) uses q(t_n + dt/2).
+ * q_knots is a host array copied at gpe_batch_create. */
+typedef struct {
+    double c0, c1, q, dt;
+    const double* q_knots;
+    int32_t n_knots;
+    double t_end;
+} gpe_params;
+
+typedef struct gpe_batch gpe_batch;
+
+/* Creates a batch over ntraj trajectories (copied; psi buffers stay caller-owned and
+ * must outlive the handle).  Trajectories of equal shape are advanced together.
+ * Allocates the handle's tables and workspace on the current device.  Errors:
+ * GPE_EINVAL (sizes, NULL or misaligned psi, dt <= 0), GPE_EUNSUPPORTED (sizes outside
+ * the ranges above), GPE_ENOMEM. */
+gpe_status gpe_batch_create(const gpe_traj* trajs, int32_t ntraj, gpe_dtype dtype,
+                            const gpe_params* params, gpe_batch** out);
+
+/* Frees the handle and its workspace (synchronises the device first). */
+gpe_status gpe_batch_destroy(gpe_batch* batch);
+
+/* Initial truncated-Wigner state (Sec. 2.2: runs start from slightly fluctuating
+ * initial conditions): psi_m(x) = mean_m + eta_m(x) for every trajectory, with
+ * mean_spinor = (re, im) of (psi_1, psi_0, psi_-1) and eta complex Gaussian,
+ * <|eta|^2> = noise_per_mode / dx^d (noise_per_mode particles per plane-wave mode).
+ * eta comes from Philox4x32-10 (Salmon et al., SC'11) keyed by the seed, counter
+ * (site mod 2^32, m, trajectory index in the batch, site >> 32), and Box-Muller in
+ * FP64.  Resets the batch time to t = 0.  Errors: GPE_EINVAL (NULL mean_spinor,
+ * noise_per_mode < 0). */
+gpe_status tw_init_noise(gpe_batch* batch, uint64_t seed, const double mean_spinor[6],
+                         double noise_per_mode, void* stream);
+
+/* Advances every trajectory by nsteps Strang steps of dt (Sec. 2.2 split-step scheme)
+ * starting from the batch time, which then increases by nsteps dt.  The fields hold
+ * psi(t) (not a half-kicked state) before and after the call.  Errors: GPE_EINVAL
+ * (nsteps < 0). */
+gpe_status gpe_step_batch(gpe_batch* batch, int64_t nsteps, void* stream);
+
+/* Observable flags. */
+#define GPE_OBS_SPECTRA 1u   /* n_1, n_0, n_-1 and S_perp, radially binned, summed over trajectories */
+#define GPE_OBS_DIAG    2u   /* per-trajectory N_1, N_0, N_-1, E_kin, E_q, E_c0, E_c1              */
+
+/* Accumulates observables of the current fields into acc (caller-owned device FP64):
+ * acc += contributions, at offset sample_slot * slot_doubles (see gpe_obs_layout).
+ * Within one slot: [4][nbins] spectra sums (quantity order n_1, n_0, n_-1, S_perp),
+ * each the sum over trajectories and over the grid modes of a bin of
+ *   n_m(k) = |A_m(k)|^2 - 1/2,  A_m(k) = dx^d / sqrt(L^d) sum_x psi_m(x) e^{-ik.x},
+ *   S_perp(k) = |F_perp(k)|^2 / L^d,  F_perp(k) = dx^d sum_x F_perp(x) e^{-ik.x},
+ *   F_perp = sqrt(2) (psi_1^* psi_0 + psi_0^* psi_-1)   (Sec. 2.1),
+ * with bin b = round(|k| / (2 pi / L)); then [ntraj][8] diagnostics (N_1, N_0, N_-1,
+ * E_kin, E_q, E_c0, E_c1, 0), E = dx^d sum_x [psi^*(-Laplacian/2)psi + q (n_1 + n_-1)
+ * + c0 rho^2 / 2 + c1 (F_z^2 + |F_perp|^2) / 2] at the current q.  Sums are
+ * deterministic (fixed reduction order).  The fields are not modified.
+ * Errors: GPE_EINVAL (NULL acc, sample_slot < 0, unknown flags), GPE_EUNSUPPORTED
+ * (spectra requested for a batch with more than one shape or unequal sides). */
+gpe_status observables_accumulate(gpe_batch* batch, double* acc, uint32_t flags,
+                                  int32_t sample_slot, void* stream);
+
+/* Accumulator geometry: number of radial bins (0 if spectra are unavailable) and the
+ * number of doubles per sample slot (4 * nbins + 8 * ntraj). */
+gpe_status gpe_obs_layout(const gpe_batch* batch, int32_t* nbins, int64_t* slot_doubles);
+
+/* Number of grid modes in each radial bin (host array of nbins int64). */
+gpe_status gpe_bin_counts(const gpe_batch* batch, int64_t* counts);
+
+/* Batch time as a step count (t = step * dt); settable for replaying segments. */
+int64_t gpe_batch_get_step(const gpe_batch* batch);
+gpe_status gpe_batch_set_step(gpe_batch* batch, int64_t step);
+
+/* Synchronises ``stream`` and returns the device status word (GPE_OK if clean) and
+ * clears it. */
+gpe_status gpe_sync_status(gpe_batch* batch, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gpe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPE_H */

@@ -1,0 +1,214 @@
+"""Thin ctypes binding of libgpe.so (include/gpe.h).  Argument marshalling only: every
+step of the split-step path runs in the library's CUDA kernels.  Torch is used for
+device memory and streams.  There is no fallback: if the library is missing, importing
+this module raises.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgpe.so")
+
+GPE_OK, GPE_EINVAL, GPE_ENOMEM, GPE_ECUDA, GPE_ETIMEOUT, GPE_ENONFINITE, GPE_EUNSUPPORTED = range(7)
+GPE_C64, GPE_C128 = 0, 1
+GPE_OBS_SPECTRA, GPE_OBS_DIAG = 1, 2
+STATUS_NAMES = {0: "GPE_OK", 1: "GPE_EINVAL", 2: "GPE_ENOMEM", 3: "GPE_ECUDA", 4: "GPE_ETIMEOUT",
+                5: "GPE_ENONFINITE", 6: "GPE_EUNSUPPORTED"}
+
+
+class gpe_traj(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("dx", ctypes.c_double),
+                ("psi", ctypes.c_void_p)]
+
+
+class gpe_params(ctypes.Structure):
+    _fields_ = [("c0", ctypes.c_double), ("c1", ctypes.c_double), ("q", ctypes.c_double),
+                ("dt", ctypes.c_double), ("q_knots", ctypes.POINTER(ctypes.c_double)),
+                ("n_knots", ctypes.c_int32), ("t_end", ctypes.c_double)]
+
+
+class GPEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i32, i64, u32, u64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.c_double)
+    pd = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "gpe_batch_create": ([ctypes.POINTER(gpe_traj), i32, ctypes.c_int, ctypes.POINTER(gpe_params),
+                              ctypes.POINTER(vp)], ctypes.c_int),
+        "gpe_batch_destroy": ([vp], ctypes.c_int),
+        "tw_init_noise": ([vp, u64, pd, dbl, vp], ctypes.c_int),
+        "gpe_step_batch": ([vp, i64, vp], ctypes.c_int),
+        "observables_accumulate": ([vp, vp, u32, i32, vp], ctypes.c_int),
+        "gpe_obs_layout": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], ctypes.c_int),
+        "gpe_bin_counts": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "gpe_batch_get_step": ([vp], i64),
+        "gpe_batch_set_step": ([vp, i64], ctypes.c_int),
+        "gpe_sync_status": ([vp, vp], ctypes.c_int),
+        "gpe_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+LIB = _load()
+
+
+def _check(status):
+    if status != GPE_OK:
+        raise GPEError(status, LIB.gpe_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------- C-ABI mirrors
+
+def gpe_batch_create(trajs, dtype, c0, c1, q, dt, q_knots=None, t_end=0.0):
+    """trajs: list of (shape, dx, psi_tensor); shape slowest axis first."""
+    arr = (gpe_traj * len(trajs))()
+    for i, (shape, dx, psi) in enumerate(trajs):
+        arr[i].ndim = len(shape)
+        n = list(reversed(shape)) + [1] * (3 - len(shape))
+        for a in range(3):
+            arr[i].n[a] = int(n[a])
+        arr[i].dx = float(dx)
+        arr[i].psi = ctypes.c_void_p(psi.data_ptr())
+    p = gpe_params(c0=float(c0), c1=float(c1), q=float(q), dt=float(dt))
+    knots_buf = None
+    if q_knots is not None:
+        knots_buf = (ctypes.c_double * len(q_knots))(*[float(x) for x in q_knots])
+        p.q_knots = knots_buf
+        p.n_knots = len(q_knots)
+        p.t_end = float(t_end)
+    h = ctypes.c_void_p()
+    _check(LIB.gpe_batch_create(arr, len(trajs), dtype, ctypes.byref(p), ctypes.byref(h)))
+    return h
+
+
+def gpe_batch_destroy(h):
+    _check(LIB.gpe_batch_destroy(h))
+
+
+def tw_init_noise(h, seed, mean_spinor, noise_per_mode, stream=None):
+    m = (ctypes.c_double * 6)(*[float(x) for x in mean_spinor])
+    _check(LIB.tw_init_noise(h, ctypes.c_uint64(int(seed)), m, float(noise_per_mode), _stream(stream)))
+
+
+def gpe_step_batch(h, nsteps, stream=None):
+    _check(LIB.gpe_step_batch(h, int(nsteps), _stream(stream)))
+
+
+def observables_accumulate(h, acc, flags, slot, stream=None):
+    assert acc.dtype == torch.float64 and acc.is_cuda and acc.is_contiguous()
+    _check(LIB.observables_accumulate(h, ctypes.c_void_p(acc.data_ptr()), int(flags), int(slot), _stream(stream)))
+
+
+def gpe_obs_layout(h):
+    nb = ctypes.c_int32()
+    sd = ctypes.c_int64()
+    _check(LIB.gpe_obs_layout(h, ctypes.byref(nb), ctypes.byref(sd)))
+    return nb.value, sd.value
+
+
+def gpe_bin_counts(h, nbins):
+    out = (ctypes.c_int64 * nbins)()
+    _check(LIB.gpe_bin_counts(h, out))
+    return np.array(out, dtype=np.int64)
+
+
+def gpe_sync_status(h, stream=None):
+    return LIB.gpe_sync_status(h, _stream(stream))
+
+
+# ----------------------------------------------------------------- convenience
+
+class GPEBatch:
+    """A batch of trajectories whose fields live in torch device tensors.
+
+    shapes: one spatial shape (uniform batch, one contiguous tensor of shape
+    (ntraj, 3, *shape)) or a list of shapes (ragged batch, one tensor each).
+    """
+
+    def __init__(self, shape, ntraj=1, dtype="c64", c0=1.0, c1=-0.1, q=0.09, dt=0.02, dx=1.0,
+                 q_knots=None, t_end=0.0, device="cuda", psi=None):
+        self.dtype = GPE_C64 if dtype == "c64" else GPE_C128
+        tdt = torch.complex64 if self.dtype == GPE_C64 else torch.complex128
+        self.dx, self.dt, self.c0, self.c1, self.q = dx, dt, c0, c1, q
+        if isinstance(shape, (list,)) and shape and isinstance(shape[0], (tuple, list)):
+            self.shapes = [tuple(s) for s in shape]
+            self.psi = [torch.zeros((3,) + s, dtype=tdt, device=device) for s in self.shapes]
+            trajs = [(s, dx, p) for s, p in zip(self.shapes, self.psi)]
+            self.uniform = False
+        else:
+            self.shapes = [tuple(shape)] * ntraj
+            if psi is None:
+                psi = torch.zeros((ntraj, 3) + tuple(shape), dtype=tdt, device=device)
+            assert psi.dtype == tdt and psi.is_contiguous() and psi.shape == (ntraj, 3) + tuple(shape)
+            self.psi = psi
+            trajs = [(tuple(shape), dx, psi[i]) for i in range(ntraj)]
+            self.uniform = True
+        self.ntraj = len(trajs)
+        self.h = gpe_batch_create(trajs, self.dtype, c0, c1, q, dt, q_knots, t_end)
+
+    def close(self):
+        if getattr(self, "h", None):
+            gpe_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_noise(self, seed, mean_spinor=(0.0, 0.0, 1.0, 0.0, 0.0, 0.0), noise_per_mode=0.5, stream=None):
+        tw_init_noise(self.h, seed, mean_spinor, noise_per_mode, stream)
+
+    def step(self, nsteps, stream=None):
+        gpe_step_batch(self.h, nsteps, stream)
+
+    def layout(self):
+        return gpe_obs_layout(self.h)
+
+    def new_accumulator(self, nslots):
+        nb, sd = self.layout()
+        return torch.zeros(nslots * sd, dtype=torch.float64, device=self.psi.device if self.uniform else self.psi[0].device)
+
+    def observables(self, acc, flags=GPE_OBS_SPECTRA | GPE_OBS_DIAG, slot=0, stream=None):
+        observables_accumulate(self.h, acc, flags, slot, stream)
+
+    def bin_counts(self):
+        nb, _ = self.layout()
+        return gpe_bin_counts(self.h, nb)
+
+    def sync_status(self, stream=None):
+        return gpe_sync_status(self.h, stream)
+
+    @property
+    def step_count(self):
+        return LIB.gpe_batch_get_step(self.h)
+
+
+def unpack_slot(acc_slot, nbins, ntraj):
+    """Split one accumulator slot into spectra (4, nbins) and diagnostics (ntraj, 8)."""
+    a = acc_slot.detach().cpu().numpy() if torch.is_tensor(acc_slot) else np.asarray(acc_slot)
+    spec = a[:4 * nbins].reshape(4, nbins) if nbins > 0 else np.zeros((4, 0))
+    diag = a[4 * max(nbins, 0):4 * max(nbins, 0) + 8 * ntraj].reshape(ntraj, 8)
+    return spec, diag

@@ -1,0 +1,235 @@
+// Batched pencil FFTs held in registers with shared-memory Stockham exchanges.
+//
+// A pencil of N = 2^p complex points is owned by TP = N / R threads; thread t holds the
+// R points x[t + m TP], m = 0..R-1 (natural order), and after the transform it holds
+// X[t + m TP].  Stages are radix R (last one radix N / R^s if R does not divide
+// evenly), each computed in registers; between stages the points go through shared
+// memory in the Stockham autosort order, so the output needs no bit reversal.  The
+// last stage of a forward transform leaves each thread with the very positions the
+// first stage of the inverse transform needs, so a momentum-space phase multiply sits
+// between them without a shared-memory round trip.
+//
+// Twiddle factors W_N^i = exp(-2 pi i i / N) come from a table computed in FP64 and
+// rounded once to T.  Transforms are unnormalised (the 1/N goes into the phase table).
+#pragma once
+
+#include "common.cuh"
+
+namespace gpe {
+
+// cos(2 pi e / 16)
+__host__ __device__ constexpr double cos16(int e) {
+    return (e & 15) == 0 ? 1.0
+         : (e & 15) == 1 ? 0.92387953251128675613
+         : (e & 15) == 2 ? 0.70710678118654752440
+         : (e & 15) == 3 ? 0.38268343236508977173
+         : (e & 15) == 4 ? 0.0
+         : (e & 15) == 5 ? -0.38268343236508977173
+         : (e & 15) == 6 ? -0.70710678118654752440
+         : (e & 15) == 7 ? -0.92387953251128675613
+         : (e & 15) == 8 ? -1.0
+         : (e & 15) == 9 ? -0.92387953251128675613
+         : (e & 15) == 10 ? -0.70710678118654752440
+         : (e & 15) == 11 ? -0.38268343236508977173
+         : (e & 15) == 12 ? 0.0
+         : (e & 15) == 13 ? 0.38268343236508977173
+         : (e & 15) == 14 ? 0.70710678118654752440
+         : 0.92387953251128675613;
+}
+
+// a * exp(DIR 2 pi i e / 16), e a compile-time constant after unrolling.
+template <int DIR, typename V>
+__device__ __forceinline__ V twc16(V a, int e) {
+    using T = decltype(a.x);
+    e &= 15;
+    if (e == 0) return a;
+    if (e == 8) return mk(-a.x, -a.y);
+    if (e == 4) return DIR < 0 ? mk(a.y, -a.x) : mk(-a.y, a.x);
+    if (e == 12) return DIR < 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
+    const double cr = cos16(e);
+    const double ci = DIR * cos16(e + 12);
+    if ((e & 1) == 0) {
+        const T h = (T)0.70710678118654752440;
+        const T xr = cr > 0 ? a.x : -a.x, yr = cr > 0 ? a.y : -a.y;
+        const T xi = ci > 0 ? a.x : -a.x, yi = ci > 0 ? a.y : -a.y;
+        return mk(h * (xr - yi), h * (xi + yr));
+    }
+    const T c = (T)cr, s = (T)ci;
+    return mk(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+// In-register DFT of size R on v[0], v[S], ..., v[(R-1) S]; natural order in and out.
+template <int R, int S, int DIR> struct Dft;
+
+template <int S, int DIR> struct Dft<1, S, DIR> {
+    template <typename V> __device__ __forceinline__ static void run(V*) {}
+};
+
+template <int S, int DIR> struct Dft<2, S, DIR> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        V a = v[0], b = v[S];
+        v[0] = cadd(a, b);
+        v[S] = csub(a, b);
+    }
+};
+
+template <int S, int DIR> struct Dft<4, S, DIR> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        V x0 = v[0], x1 = v[S], x2 = v[2 * S], x3 = v[3 * S];
+        V a0 = cadd(x0, x2), a1 = csub(x0, x2), a2 = cadd(x1, x3);
+        V a3 = twc16<DIR>(csub(x1, x3), 4);
+        v[0] = cadd(a0, a2);
+        v[2 * S] = csub(a0, a2);
+        v[S] = cadd(a1, a3);
+        v[3 * S] = csub(a1, a3);
+    }
+};
+
+// R = R1 * R2: n = R2 n1 + n2, k = k1 + R1 k2.
+template <int R, int S, int DIR> struct Dft {
+    static constexpr int R1 = (R == 8) ? 2 : 4;
+    static constexpr int R2 = R / R1;
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) Dft<R1, R2 * S, DIR>::run(v + n2 * S);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1)
+#pragma unroll
+            for (int n2 = 1; n2 < R2; ++n2)
+                v[(R2 * k1 + n2) * S] = twc16<DIR>(v[(R2 * k1 + n2) * S], (16 / R) * n2 * k1);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) Dft<R2, S, DIR>::run(v + R2 * k1 * S);
+        V tmp[R];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) tmp[k1 + R1 * k2] = v[(R2 * k1 + k2) * S];
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k * S] = tmp[k];
+    }
+};
+
+// Padded shared-memory index: one spare slot every 16 elements.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+
+// Shared-memory length per pencil buffer: padded length, rounded so consecutive pencil
+// buffers start one 8-byte (float2) / 16-byte (double2) bank slot apart.
+template <typename T>
+__host__ __device__ constexpr int smem_ld(int n) {
+    return ((n + n / 16 + (int)(128 / (2 * sizeof(T))) - 1) / (int)(128 / (2 * sizeof(T)))) *
+               (int)(128 / (2 * sizeof(T))) + 1;
+}
+
+enum class Sync { Block, Warp };
+
+template <Sync SY> __device__ __forceinline__ void pencil_sync() {
+    if constexpr (SY == Sync::Block) __syncthreads();
+    else __syncwarp(blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u));
+}
+
+// Stage plan of a length-N transform with R points per thread: stages of radix R, then
+// one of radix N / R^s if needed.  Stage s combines sub-transforms of length NS(s).
+// Twiddles of stage s (NS > 1) are stored as a block [r = 1..RS-1][k = 0..NS-1] of
+// W_{NS RS}^{r k}, so threads with consecutive k read consecutive entries.
+template <int N, int R>
+struct FftPlan {
+    static constexpr int kLogN = ilog2(N), kLogR = ilog2(R);
+    static constexpr int kFull = kLogN / kLogR;
+    static constexpr int kLast = 1 << (kLogN - kFull * kLogR);
+    static constexpr int kStages = kFull + (kLast > 1 ? 1 : 0);
+    static constexpr int radix(int s) { return s < kFull ? R : kLast; }
+    static constexpr int ns(int s) {
+        int v = 1;
+        for (int i = 0; i < s; ++i) v *= radix(i);
+        return v;
+    }
+    static constexpr int tw_offset(int s) {
+        int off = 0;
+        for (int i = 0; i < s; ++i)
+            if (ns(i) > 1) off += (radix(i) - 1) * ns(i);
+        return off;
+    }
+    static constexpr int tw_size() { return tw_offset(kStages); }
+};
+
+// One Stockham stage S of radix RS on sub-transforms of length NS.
+template <int N, int R, int DIR, int NC, int S, Sync SY, typename V>
+__device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC],
+                                               const V* __restrict__ tws, int t) {
+    using P = FftPlan<N, R>;
+    constexpr int TP = N / R;
+    constexpr int RS = P::radix(S);
+    constexpr int NS = P::ns(S);
+    constexpr bool LAST = (S == P::kStages - 1);
+    constexpr int B = R / RS;
+    constexpr int OFF = P::tw_offset(S);
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const int j = t + u * TP;
+        const int k = j & (NS - 1);
+        V w[NC][RS];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int r = 0; r < RS; ++r) w[c][r] = v[c][u + r * B];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < RS; ++r) {
+                V f = tws[OFF + (r - 1) * NS + k];
+                if (DIR > 0) f = cconj(f);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) w[c][r] = cmul(w[c][r], f);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Dft<RS, 1, DIR>::run(w[c]);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int r = 0; r < RS; ++r) v[c][u + r * B] = w[c][r];
+        } else {
+            const int base = (j - k) * RS + k;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int r = 0; r < RS; ++r) buf[c][spad(base + r * NS)] = w[c][r];
+        }
+    }
+    if constexpr (!LAST) {
+        pencil_sync<SY>();
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[c][m] = buf[c][spad(t + m * TP)];
+        pencil_sync<SY>();
+    }
+}
+
+template <int N, int R, int DIR, int NC, int S, Sync SY, typename V>
+__device__ __forceinline__ void stockham_from(V (&v)[NC][R], V* const (&buf)[NC],
+                                              const V* __restrict__ tws, int t) {
+    if constexpr (S < FftPlan<N, R>::kStages) {
+        stockham_stage<N, R, DIR, NC, S, SY>(v, buf, tws, t);
+        stockham_from<N, R, DIR, NC, S + 1, SY>(v, buf, tws, t);
+    }
+}
+
+// Length-N transform of NC pencils at once (one per component), DIR = -1 forward
+// (e^{-2 pi i jk/N}), +1 inverse (unnormalised).  Every thread of the sync group must
+// call it.  buf[c]: shared buffer of pencil c (smem_ld<T>(N) elements); tws: the stage
+// twiddle table of FftPlan<N, R> (usually a shared-memory copy).
+template <int N, int R, int DIR, int NC, Sync SY, typename V>
+__device__ __forceinline__ void fft_pencil(V (&v)[NC][R], V* const (&buf)[NC],
+                                           const V* __restrict__ tws, int t) {
+    static_assert((N & (N - 1)) == 0 && N >= R, "N must be a power of two >= R");
+    stockham_from<N, R, DIR, NC, 0, SY>(v, buf, tws, t);
+}
+
+// Cooperative copy of a table into shared memory (caller synchronises).
+template <typename V>
+__device__ __forceinline__ void copy_table(V* dst, const V* __restrict__ src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+}  // namespace gpe

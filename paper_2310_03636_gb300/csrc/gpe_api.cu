@@ -1,0 +1,432 @@
+// C-ABI layer: argument checks, handle (tables, groups, workspace), dispatch of the
+// split-step passes, status word.  Declarations and contracts: include/gpe.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "gpe.h"
+#include "internal.h"
+#include "obs.h"
+
+using namespace gpe;
+
+namespace {
+
+thread_local std::string g_err;
+
+gpe_status fail(gpe_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define GPE_CK(call)                                                                      \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return fail(GPE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+struct gpe_batch {
+    gpe_dtype dtype;
+    gpe_params p;
+    std::vector<double> knots;
+    double* d_knots = nullptr;
+    std::vector<gpe_traj> trajs;
+    std::vector<Group> groups;
+    int64_t step = 0;
+    int* d_status = nullptr;
+    int device = 0;
+    std::vector<void*> allocs;
+    ObsWork obs;
+};
+
+namespace {
+
+// Kinetic phase tables exp(-i tau k^2/2) / n for tau = dt and dt/2, computed in FP64.
+template <typename T>
+void phase_tables_host(int n, double dx, double dt, std::vector<cplx<T>>& pf, std::vector<cplx<T>>& ph) {
+    pf.resize(n);
+    ph.resize(n);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int i = 0; i < n; ++i) {
+        const int j = (i < n / 2) ? i : i - n;
+        const double k = two_pi * (double)j / ((double)n * dx);
+        const double a_full = 0.5 * dt * k * k, a_half = 0.25 * dt * k * k;
+        pf[i] = mk((T)(std::cos(a_full) / n), (T)(-std::sin(a_full) / n));
+        ph[i] = mk((T)(std::cos(a_half) / n), (T)(-std::sin(a_half) / n));
+    }
+}
+
+// Stage twiddle table of a length-n transform with R points per thread, laid out as the
+// device-side FftPlan<n, R> expects: for each stage with sub-length ns > 1 and radix rs,
+// a block [r = 1..rs-1][k = 0..ns-1] of exp(-2 pi i r k / (ns rs)), computed in FP64.
+template <typename T>
+std::vector<cplx<T>> stage_twiddles_host(int n, int R) {
+    int logn = 0, logr = 0;
+    while ((1 << logn) < n) ++logn;
+    while ((1 << logr) < R) ++logr;
+    const int nfull = logn / logr;
+    const int last = 1 << (logn - nfull * logr);
+    const int stages = nfull + (last > 1 ? 1 : 0);
+    std::vector<cplx<T>> out;
+    const double two_pi = 6.283185307179586476925286766559;
+    int ns = 1;
+    for (int s = 0; s < stages; ++s) {
+        const int rs = (s < nfull) ? R : last;
+        if (ns > 1)
+            for (int r = 1; r < rs; ++r)
+                for (int k = 0; k < ns; ++k) {
+                    const double ang = two_pi * (double)r * (double)k / ((double)ns * rs);
+                    out.push_back(mk((T)std::cos(ang), (T)(-std::sin(ang))));
+                }
+        ns *= rs;
+    }
+    if (out.empty()) out.push_back(mk((T)1, (T)0));
+    return out;
+}
+
+gpe_status dev_alloc(gpe_batch* b, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GPE_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    b->allocs.push_back(*p);
+    return GPE_OK;
+}
+
+template <typename T>
+gpe_status build_group_tables(gpe_batch* b, Group& g) {
+    for (int a = 0; a < g.ndim; ++a) {
+        std::vector<cplx<T>> pf, ph;
+        phase_tables_host<T>(g.n[a], g.dx, b->p.dt, pf, ph);
+        const size_t bytes = sizeof(cplx<T>) * g.n[a];
+        gpe_status s;
+        if ((s = dev_alloc(b, &g.ph_full[a], bytes)) != GPE_OK) return s;
+        if ((s = dev_alloc(b, &g.ph_half[a], bytes)) != GPE_OK) return s;
+        GPE_CK(cudaMemcpy(g.ph_full[a], pf.data(), bytes, cudaMemcpyHostToDevice));
+        GPE_CK(cudaMemcpy(g.ph_half[a], ph.data(), bytes, cudaMemcpyHostToDevice));
+        for (int ri = 0; ri < 3; ++ri) {
+            const std::vector<cplx<T>> tw = stage_twiddles_host<T>(g.n[a], 4 << ri);
+            const size_t tb = sizeof(cplx<T>) * tw.size();
+            if ((s = dev_alloc(b, &g.tw[a][ri], tb)) != GPE_OK) return s;
+            GPE_CK(cudaMemcpy(g.tw[a][ri], tw.data(), tb, cudaMemcpyHostToDevice));
+        }
+    }
+    return GPE_OK;
+}
+
+template <typename T>
+gpe_status check_sizes(const gpe_traj& t) {
+    if (t.ndim == 1) {
+        if (t.n[0] < 64 || t.n[0] > resident1d_max_n<T>())
+            return fail(GPE_EUNSUPPORTED, "1D size %d outside [64, %d]", t.n[0], resident1d_max_n<T>());
+    } else {
+        for (int a = 0; a < t.ndim; ++a) {
+            const int lim = (a == 0) ? xpass_max_n<T>() : colpass_max_n<T>();
+            if (t.n[a] < 64 || t.n[a] > lim)
+                return fail(GPE_EUNSUPPORTED, "axis %d size %d outside [64, %d]", a, t.n[a], lim);
+        }
+    }
+    return GPE_OK;
+}
+
+double q_at_host(const gpe_batch* b, double t) {
+    const int K = b->p.n_knots;
+    if (K <= 0) return b->p.q;
+    if (K == 1) return b->knots[0];
+    double u = t / b->p.t_end * (double)(K - 1);
+    if (u <= 0.0) return b->knots[0];
+    if (u >= (double)(K - 1)) return b->knots[K - 1];
+    int i = (int)std::floor(u);
+    double w = u - (double)i;
+    return b->knots[i] * (1.0 - w) + b->knots[i + 1] * w;
+}
+
+template <typename T>
+PassArgs<T> base_args(const gpe_batch* b, const Group& g) {
+    PassArgs<T> a{};
+    a.ptrs = reinterpret_cast<cplx<T>* const*>(g.dptrs);
+    a.comp_stride = g.sites;
+    a.ntraj = g.ntraj;
+    a.ncomp = 3;
+    a.coef.c0 = (T)b->p.c0;
+    a.coef.c1 = (T)b->p.c1;
+    a.coef.dt = (T)b->p.dt;
+    a.coef.q = (T)b->p.q;
+    return a;
+}
+
+// Pure kinetic pass along axis ax (1 = y, 2 = z) with the full or half time step.
+template <typename T>
+cudaError_t col_pass(const gpe_batch* b, const Group& g, int ax, bool half, cudaStream_t s) {
+    PassArgs<T> a = base_args<T>(b, g);
+    for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const cplx<T>*>(g.tw[ax][ri]);
+    a.ph = reinterpret_cast<const cplx<T>*>(half ? g.ph_half[ax] : g.ph_full[ax]);
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    if (ax == 1) {
+        a.stride = nx;
+        a.n_outer = nz;
+        a.outer_stride = (int64_t)nx * ny;
+    } else {
+        a.stride = (int64_t)nx * ny;
+        a.n_outer = ny;
+        a.outer_stride = nx;
+    }
+    a.nx_tiles = nx / colpass_cols<T>(g.n[ax]);
+    return launch_colpass<T>(g.n[ax], a, s);
+}
+
+template <typename T>
+cudaError_t x_pass(const gpe_batch* b, const Group& g, bool pre, bool half_post, double q, cudaStream_t s) {
+    PassArgs<T> a = base_args<T>(b, g);
+    for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const cplx<T>*>(g.tw[0][ri]);
+    a.ph_pre = reinterpret_cast<const cplx<T>*>(g.ph_half[0]);
+    a.ph = reinterpret_cast<const cplx<T>*>(half_post ? g.ph_half[0] : g.ph_full[0]);
+    a.rows_per_traj = (int64_t)g.n[1] * g.n[2];
+    a.total_rows = a.rows_per_traj * g.ntraj;
+    a.coef.q = (T)q;
+    return launch_xpass<T>(g.n[0], pre, a, s);
+}
+
+template <typename T>
+gpe_status step_group(gpe_batch* b, const Group& g, int64_t nsteps, cudaStream_t s) {
+    const double dt = b->p.dt;
+    const double t0 = (double)b->step * dt;
+    if (g.ndim == 1) {
+        Res1DArgs<T> a{};
+        a.ptrs = reinterpret_cast<cplx<T>* const*>(g.dptrs);
+        a.ntraj = g.ntraj;
+        for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const cplx<T>*>(g.tw[0][ri]);
+        a.ph_full = reinterpret_cast<const cplx<T>*>(g.ph_full[0]);
+        a.ph_half = reinterpret_cast<const cplx<T>*>(g.ph_half[0]);
+        a.c0 = (T)b->p.c0;
+        a.c1 = (T)b->p.c1;
+        a.dt = (T)dt;
+        a.dt_d = dt;
+        a.t0 = t0;
+        a.q_const = b->p.q;
+        a.t_end = b->p.t_end;
+        a.knots = b->d_knots;
+        a.n_knots = b->p.n_knots;
+        a.nsteps = nsteps;
+        GPE_CK(launch_resident1d<T>(g.n[0], a, s));
+        return GPE_OK;
+    }
+    // K(dt/2) along the strided axes first (they commute with the x pass), then per step
+    // an x pass [Kx(dt/2) on the first step] L Kx(dt or dt/2) and the strided passes.
+    for (int ax = g.ndim - 1; ax >= 1; --ax) GPE_CK(col_pass<T>(b, g, ax, true, s));
+    for (int64_t st = 0; st < nsteps; ++st) {
+        const bool last = (st == nsteps - 1);
+        const double q = q_at_host(b, t0 + ((double)st + 0.5) * dt);
+        GPE_CK(x_pass<T>(b, g, st == 0, last, q, s));
+        for (int ax = 1; ax < g.ndim; ++ax) GPE_CK(col_pass<T>(b, g, ax, last, s));
+    }
+    return GPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gpe_last_error(void) { return g_err.c_str(); }
+
+gpe_status gpe_batch_create(const gpe_traj* trajs, int32_t ntraj, gpe_dtype dtype, const gpe_params* params,
+                            gpe_batch** out) {
+    g_err.clear();
+    if (!out) return fail(GPE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!trajs || ntraj <= 0) return fail(GPE_EINVAL, "need ntraj > 0 trajectories");
+    if (!params) return fail(GPE_EINVAL, "params is NULL");
+    if (dtype != GPE_C64 && dtype != GPE_C128) return fail(GPE_EINVAL, "unknown dtype %d", (int)dtype);
+    if (!(params->dt > 0.0) || !std::isfinite(params->dt)) return fail(GPE_EINVAL, "dt must be > 0");
+    if (!std::isfinite(params->c0) || !std::isfinite(params->c1) || !std::isfinite(params->q))
+        return fail(GPE_EINVAL, "non-finite coupling");
+    if (params->n_knots < 0 || (params->n_knots > 0 && !params->q_knots))
+        return fail(GPE_EINVAL, "bad q knots");
+    if (params->n_knots > 1 && !(params->t_end > 0.0)) return fail(GPE_EINVAL, "t_end must be > 0 with knots");
+    for (int i = 0; i < ntraj; ++i) {
+        const gpe_traj& t = trajs[i];
+        if (t.ndim < 1 || t.ndim > 3) return fail(GPE_EINVAL, "traj %d: ndim %d", i, t.ndim);
+        for (int a = 0; a < 3; ++a) {
+            if (a < t.ndim && !is_pow2(t.n[a])) return fail(GPE_EINVAL, "traj %d: n[%d]=%d not a power of two", i, a, t.n[a]);
+            if (a >= t.ndim && t.n[a] != 1) return fail(GPE_EINVAL, "traj %d: unused n[%d] must be 1", i, a);
+        }
+        if (!(t.dx > 0.0)) return fail(GPE_EINVAL, "traj %d: dx must be > 0", i);
+        if (!t.psi || ((uintptr_t)t.psi & 15u)) return fail(GPE_EINVAL, "traj %d: psi NULL or not 16-byte aligned", i);
+        gpe_status s = (dtype == GPE_C64) ? check_sizes<float>(t) : check_sizes<double>(t);
+        if (s != GPE_OK) return s;
+    }
+    gpe_batch* b = new (std::nothrow) gpe_batch();
+    if (!b) return fail(GPE_ENOMEM, "host allocation failed");
+    b->dtype = dtype;
+    b->p = *params;
+    if (params->n_knots > 0) b->knots.assign(params->q_knots, params->q_knots + params->n_knots);
+    b->p.q_knots = nullptr;
+    b->trajs.assign(trajs, trajs + ntraj);
+    cudaGetDevice(&b->device);
+    auto cleanup = [&](gpe_status s) {
+        gpe_batch_destroy(b);
+        return s;
+    };
+    gpe_status s;
+    if ((s = dev_alloc(b, (void**)&b->d_status, sizeof(int))) != GPE_OK) return cleanup(s);
+    if (cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) return cleanup(fail(GPE_ECUDA, "memset status"));
+    if (!b->knots.empty()) {
+        if ((s = dev_alloc(b, (void**)&b->d_knots, sizeof(double) * b->knots.size())) != GPE_OK) return cleanup(s);
+        if (cudaMemcpy(b->d_knots, b->knots.data(), sizeof(double) * b->knots.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(GPE_ECUDA, "copy knots"));
+    }
+    // group trajectories of equal shape and spacing
+    std::map<std::tuple<int, int, int, int, double>, int> gi;
+    for (int i = 0; i < ntraj; ++i) {
+        const gpe_traj& t = trajs[i];
+        auto key = std::make_tuple(t.ndim, t.n[0], t.n[1], t.n[2], t.dx);
+        auto it = gi.find(key);
+        int k;
+        if (it == gi.end()) {
+            k = (int)b->groups.size();
+            gi[key] = k;
+            Group g;
+            g.ndim = t.ndim;
+            g.n[0] = t.n[0];
+            g.n[1] = t.n[1];
+            g.n[2] = t.n[2];
+            g.dx = t.dx;
+            g.sites = (int64_t)t.n[0] * t.n[1] * t.n[2];
+            b->groups.push_back(g);
+        } else {
+            k = it->second;
+        }
+        b->groups[k].ids.push_back(i);
+        b->groups[k].hptrs.push_back(t.psi);
+    }
+    for (Group& g : b->groups) {
+        g.ntraj = (int)g.ids.size();
+        if ((s = dev_alloc(b, (void**)&g.dptrs, sizeof(void*) * g.ntraj)) != GPE_OK) return cleanup(s);
+        if ((s = dev_alloc(b, (void**)&g.d_ids, sizeof(int32_t) * g.ntraj)) != GPE_OK) return cleanup(s);
+        if (cudaMemcpy(g.dptrs, g.hptrs.data(), sizeof(void*) * g.ntraj, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(g.d_ids, g.ids.data(), sizeof(int32_t) * g.ntraj, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(GPE_ECUDA, "copy group tables"));
+        s = (dtype == GPE_C64) ? build_group_tables<float>(b, g) : build_group_tables<double>(b, g);
+        if (s != GPE_OK) return cleanup(s);
+    }
+    if ((s = obs_init(b->obs, b->groups, b->dtype == GPE_C128, b->device)) != GPE_OK) {
+        g_err = obs_last_error();
+        return cleanup(s);
+    }
+    *out = b;
+    return GPE_OK;
+}
+
+gpe_status gpe_batch_destroy(gpe_batch* b) {
+    if (!b) return GPE_OK;
+    cudaDeviceSynchronize();
+    obs_free(b->obs);
+    for (void* p : b->allocs) cudaFree(p);
+    delete b;
+    return GPE_OK;
+}
+
+gpe_status tw_init_noise(gpe_batch* b, uint64_t seed, const double mean_spinor[6], double noise_per_mode,
+                         void* stream) {
+    g_err.clear();
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    if (!mean_spinor) return fail(GPE_EINVAL, "mean_spinor is NULL");
+    if (!(noise_per_mode >= 0.0) || !std::isfinite(noise_per_mode)) return fail(GPE_EINVAL, "noise_per_mode must be >= 0");
+    for (int i = 0; i < 6; ++i)
+        if (!std::isfinite(mean_spinor[i])) return fail(GPE_EINVAL, "non-finite mean spinor");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (const Group& g : b->groups) {
+        NoiseArgs a{};
+        a.ptrs = g.dptrs;
+        a.traj_ids = g.d_ids;
+        a.ntraj = g.ntraj;
+        a.sites = g.sites;
+        a.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+        a.key1 = (uint32_t)(seed >> 32);
+        a.sigma = std::sqrt(noise_per_mode / std::pow(g.dx, g.ndim));
+        for (int i = 0; i < 6; ++i) a.mean[i] = mean_spinor[i];
+        GPE_CK(b->dtype == GPE_C64 ? launch_noise<float>(a, s) : launch_noise<double>(a, s));
+    }
+    b->step = 0;
+    return GPE_OK;
+}
+
+gpe_status gpe_step_batch(gpe_batch* b, int64_t nsteps, void* stream) {
+    g_err.clear();
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    if (nsteps < 0) return fail(GPE_EINVAL, "nsteps < 0");
+    if (nsteps == 0) return GPE_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (const Group& g : b->groups) {
+        gpe_status st = (b->dtype == GPE_C64) ? step_group<float>(b, g, nsteps, s) : step_group<double>(b, g, nsteps, s);
+        if (st != GPE_OK) return st;
+    }
+    b->step += nsteps;
+    return GPE_OK;
+}
+
+gpe_status observables_accumulate(gpe_batch* b, double* acc, uint32_t flags, int32_t slot, void* stream) {
+    g_err.clear();
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    if (!acc) return fail(GPE_EINVAL, "acc is NULL");
+    if (slot < 0) return fail(GPE_EINVAL, "sample_slot < 0");
+    if (flags & ~(GPE_OBS_SPECTRA | GPE_OBS_DIAG)) return fail(GPE_EINVAL, "unknown flags 0x%x", flags);
+    if ((flags & GPE_OBS_SPECTRA) && b->obs.nbins <= 0)
+        return fail(GPE_EUNSUPPORTED, "spectra need one shape with equal side lengths");
+    const double q = q_at_host(b, (double)b->step * b->p.dt);
+    gpe_status s = obs_accumulate(b->obs, b->groups, b->dtype == GPE_C128, b->p.c0, b->p.c1, q, acc, flags, slot,
+                                  b->d_status, (cudaStream_t)stream);
+    if (s != GPE_OK) g_err = obs_last_error();
+    return s;
+}
+
+gpe_status gpe_obs_layout(const gpe_batch* b, int32_t* nbins, int64_t* slot_doubles) {
+    if (!b || !nbins || !slot_doubles) return fail(GPE_EINVAL, "NULL argument");
+    *nbins = b->obs.nbins;
+    *slot_doubles = (int64_t)4 * (b->obs.nbins > 0 ? b->obs.nbins : 0) + 8 * (int64_t)b->trajs.size();
+    return GPE_OK;
+}
+
+gpe_status gpe_bin_counts(const gpe_batch* b, int64_t* counts) {
+    if (!b || !counts) return fail(GPE_EINVAL, "NULL argument");
+    if (b->obs.nbins <= 0) return fail(GPE_EUNSUPPORTED, "no radial bins for this batch");
+    std::memcpy(counts, b->obs.counts.data(), sizeof(int64_t) * b->obs.nbins);
+    return GPE_OK;
+}
+
+int64_t gpe_batch_get_step(const gpe_batch* b) { return b ? b->step : -1; }
+
+gpe_status gpe_batch_set_step(gpe_batch* b, int64_t step) {
+    if (!b || step < 0) return fail(GPE_EINVAL, "bad batch or step");
+    b->step = step;
+    return GPE_OK;
+}
+
+gpe_status gpe_sync_status(gpe_batch* b, void* stream) {
+    g_err.clear();
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    GPE_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    int st = 0;
+    GPE_CK(cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    GPE_CK(cudaMemset(b->d_status, 0, sizeof(int)));
+    if (st != 0) return fail((gpe_status)st, "device status %d", st);
+    return GPE_OK;
+}
+
+}  // extern "C"

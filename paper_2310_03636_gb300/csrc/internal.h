@@ -1,0 +1,96 @@
+// Internal (non-ABI) declarations shared by the kernel translation units and the C-ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "local_step.cuh"
+
+namespace gpe {
+
+// Arguments of the axis passes.  A "row" pass works on pencils along x (contiguous),
+// all three components of a site together; a "column" pass works on pencils along y or
+// z (stride ``stride`` elements), one component at a time, COLS adjacent x columns per
+// block.
+template <typename T>
+struct PassArgs {
+    cplx<T>* const* ptrs;     // per trajectory of the group: field base pointer
+    int64_t comp_stride;      // elements between components (= sites per trajectory)
+    int64_t rows_per_traj;    // row pass: ny * nz
+    int64_t total_rows;       // row pass: ntraj * rows_per_traj
+    int64_t stride;           // column pass: elements between consecutive pencil points
+    int64_t outer_stride;     // column pass: elements between consecutive outer indices
+    int32_t n_outer;          // column pass: number of outer indices (z for a y pass, y for a z pass)
+    int32_t nx_tiles;         // column pass: nx / COLS
+    int32_t ntraj;
+    int32_t ncomp;            // column pass: fields per trajectory (3, or 4 for spectra work)
+    const cplx<T>* tw[3];     // stage twiddle tables of the axis for R = 4, 8, 16 points per thread
+    const cplx<T>* ph_pre;    // row pass with a leading half kinetic step: its phase table
+    const cplx<T>* ph;        // phase table exp(-i tau k^2 / 2) / N
+    LocalCoef<T> coef;        // couplings for the local step (row pass)
+};
+
+template <typename T>
+struct Res1DArgs {
+    cplx<T>* const* ptrs;
+    int32_t ntraj;
+    const cplx<T>* tw[3];     // stage twiddle tables for R = 4, 8, 16
+    const cplx<T>* ph_full;   // tau = dt
+    const cplx<T>* ph_half;   // tau = dt / 2
+    T c0, c1, dt;
+    double dt_d, t0, q_const, t_end;
+    const double* knots;      // device, may be null
+    int32_t n_knots;
+    int64_t nsteps;
+};
+
+struct NoiseArgs {
+    void* const* ptrs;        // per trajectory field pointer
+    const int32_t* traj_ids;  // batch index of each trajectory (Philox counter word 2)
+    int32_t ntraj;
+    int64_t sites;
+    uint32_t key0, key1;
+    double sigma;             // sqrt(noise_per_mode / dx^d)
+    double mean[6];
+};
+
+// Trajectories of one shape and spacing, advanced together.
+struct Group {
+    int ndim = 1;
+    int n[3] = {1, 1, 1};
+    double dx = 1.0;
+    int64_t sites = 0;
+    int ntraj = 0;
+    std::vector<int> ids;          // batch index of each member
+    std::vector<void*> hptrs;      // field pointers (device addresses)
+    void** dptrs = nullptr;        // same, on the device
+    int32_t* d_ids = nullptr;      // same as ids, on the device
+    void* tw[3][3] = {};           // per axis: stage twiddle tables for R = 4, 8, 16
+    void* ph_full[3] = {};         // per axis: exp(-i dt k^2/2)/n
+    void* ph_half[3] = {};         // per axis: exp(-i dt k^2/4)/n
+};
+
+template <typename T> int xpass_max_n();
+template <typename T> int colpass_max_n();
+template <typename T> int resident1d_max_n();
+
+template <typename T>
+cudaError_t launch_xpass(int n, bool pre, const PassArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_colpass(int n, const PassArgs<T>& a, cudaStream_t s);
+// Forward transform only (no phase, no inverse): used on spectra workspaces.
+template <typename T>
+cudaError_t launch_colfft(int n, const PassArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rowfft(int n, cplx<T>* data, int64_t rows, const cplx<T>* const* tw, cudaStream_t s);
+template <typename T>
+int colpass_cols(int n);
+template <typename T>
+cudaError_t launch_resident1d(int n, const Res1DArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_noise(const NoiseArgs& a, cudaStream_t s);
+
+}  // namespace gpe

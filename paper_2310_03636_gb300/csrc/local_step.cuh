@@ -1,0 +1,88 @@
+// Per-site nonlinear part of the split step: L(dt) = D(dt/2) O(dt) D(dt/2).
+//
+// D (diagonal step of Sec. 2.2): psi_m <- psi_m exp(-i f_m tau) with the diagonal
+// entries of the operator of Eq. (GPE) (V = 0):
+//   f_1  = q + (c0 + c1) rho - 2 c1 |psi_-1|^2
+//   f_0  =     (c0 + c1) rho -   c1 |psi_0|^2        (q - c1 q / c1 = 0)
+//   f_-1 = q + (c0 + c1) rho - 2 c1 |psi_1|^2
+// evaluated on the field D acts on (D leaves every density unchanged, so it is exact).
+//
+// O (off-diagonal step of Sec. 2.2): with S = [[0, a, 0], [a*, 0, b], [0, b*, 0]],
+// a = psi_-1^* psi_0, b = psi_0^* psi_1, the predictor psi~ = psi - i c1 dt S psi, and
+// the averages A = (a + a~)/2, B = (b + b~)/2, the printed 3x3 matrix equals
+//   U = exp(-i c1 dt S_AB) = 1 - i (sin th / lambda) S_AB + ((cos th - 1) / lambda^2) S_AB^2,
+// th = lambda c1 dt, lambda^2 = |A|^2 + |B|^2 (S_AB^3 = lambda^2 S_AB).  The kernel
+// applies it as psi - i eps s1 S psi - eps^2 s2 S (S psi) with eps = c1 dt,
+// s1 = sin(th)/th and s2 = (1 - cos th)/th^2 = sinc^2(th/2)/2, both from one sincos of
+// th/2, which is finite and accurate down to lambda = 0 (where U = 1).  The paper's
+// form divides by lambda^2; this one does not, and is algebraically identical.
+#pragma once
+
+#include "common.cuh"
+
+namespace gpe {
+
+template <typename T>
+struct LocalCoef {
+    T c0, c1, q, dt;
+};
+
+template <typename T, typename V>
+__device__ __forceinline__ void diag_phase(V& p1, V& p0, V& pm, T c0, T c1, T q, T tau) {
+    const T n1 = cabs2(p1), n0 = cabs2(p0), nm = cabs2(pm);
+    const T g = (c0 + c1) * (n1 + n0 + nm);
+    const T th1 = (q + g - (T)2 * c1 * nm) * tau;
+    const T th0 = (g - c1 * n0) * tau;
+    const T thm = (q + g - (T)2 * c1 * n1) * tau;
+    T s, c;
+    sincos_t(th1, &s, &c);
+    p1 = mk(p1.x * c + p1.y * s, p1.y * c - p1.x * s);
+    sincos_t(th0, &s, &c);
+    p0 = mk(p0.x * c + p0.y * s, p0.y * c - p0.x * s);
+    sincos_t(thm, &s, &c);
+    pm = mk(pm.x * c + pm.y * s, pm.y * c - pm.x * s);
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void offdiag_mix(V& p1, V& p0, V& pm, T c1, T dt) {
+    const T eps = c1 * dt;
+    const V a = cmulc(pm, p0);   // psi_-1^* psi_0
+    const V b = cmulc(p0, p1);   // psi_0^* psi_1
+    // predictor psi~ = psi - i eps S psi
+    const V s1 = cmul(a, p0);
+    const V s0 = cadd(cmulc(a, p1), cmul(b, pm));
+    const V sm = cmulc(b, p0);
+    const V t1 = csub(p1, cscale(mk(-s1.y, s1.x), eps));
+    const V t0 = csub(p0, cscale(mk(-s0.y, s0.x), eps));
+    const V tm = csub(pm, cscale(mk(-sm.y, sm.x), eps));
+    const V A = cscale(cadd(a, cmulc(tm, t0)), (T)0.5);
+    const V B = cscale(cadd(b, cmulc(t0, t1)), (T)0.5);
+    const T lam = sqrt_t(cabs2(A) + cabs2(B));
+    const T x = (T)0.5 * lam * eps;   // th / 2
+    T sx, cx;
+    sincos_t(x, &sx, &cx);
+    const T r = (x != (T)0) ? sx / x : (T)1;   // sinc(th/2)
+    const T e1 = eps * r * cx;                 // eps sin(th)/th
+    const T e2 = (T)0.5 * eps * eps * r * r;   // eps^2 (1 - cos th)/th^2
+    // S_AB psi and S_AB^2 psi
+    const V u1 = cmul(A, p0);
+    const V u0 = cadd(cmulc(A, p1), cmul(B, pm));
+    const V um = cmulc(B, p0);
+    const V w1 = cmul(A, u0);
+    const V w0 = cadd(cmulc(A, u1), cmul(B, um));
+    const V wm = cmulc(B, u0);
+    // psi - i e1 u - e2 w
+    p1 = mk(p1.x + e1 * u1.y - e2 * w1.x, p1.y - e1 * u1.x - e2 * w1.y);
+    p0 = mk(p0.x + e1 * u0.y - e2 * w0.x, p0.y - e1 * u0.x - e2 * w0.y);
+    pm = mk(pm.x + e1 * um.y - e2 * wm.x, pm.y - e1 * um.x - e2 * wm.y);
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ void local_step(V& p1, V& p0, V& pm, const LocalCoef<T>& k) {
+    const T h = (T)0.5 * k.dt;
+    diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h);
+    offdiag_mix<T>(p1, p0, pm, k.c1, k.dt);
+    diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h);
+}
+
+}  // namespace gpe

@@ -1,0 +1,343 @@
+// Observables pipeline (sample times only; the fields are read, never written):
+//   1. k_obs_prep   real space, per site: copy psi_m and F_perp = sqrt2 (psi_1^* psi_0 +
+//                   psi_0^* psi_-1) into a 4-field workspace; FP64 partial sums of N_m,
+//                   q (n_1 + n_-1), c0 rho^2 / 2, c1 (F_z^2 + |F_perp|^2) / 2 per site block;
+//   2. forward FFTs of the 4 fields along every axis (same pencil FFT as the propagation);
+//   3. k_obs_ekin   FP64 partial sums of (k^2/2) |psi_m(k)|^2 per mode block;
+//   4. k_obs_bins   per (radial bin, field): sum over trajectories and the bin's modes of
+//                   |W|^2 dx^d / N (- 1/2 for the occupations), FP64, into the caller's
+//                   accumulator;
+//   5. k_obs_final  per trajectory: the partial sums in fixed order into the accumulator.
+// Every reduction has a fixed order (per-thread strided sums, shuffle trees, warp sums
+// combined in index order), so results are bitwise reproducible.
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "obs.h"
+
+namespace gpe {
+
+namespace {
+
+thread_local std::string g_obs_err;
+
+constexpr int kThreads = 256;
+constexpr int kSitesPerBlock = 4096;
+
+gpe_status obs_fail(gpe_status s, const char* what, cudaError_t e) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    g_obs_err = buf;
+    return s;
+}
+
+// Fixed-order block sum of NV doubles per thread; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV * 32 */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sm[k * 32 + warp] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sm[k * 32 + w];
+            v[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_obs_prep(cplx<T>* const* __restrict__ ptrs, int t0, cplx<T>* __restrict__ W, int64_t sites, double c0,
+           double c1, double q, double* __restrict__ part, int64_t nblk) {
+    using V = cplx<T>;
+    __shared__ double sm[6 * 32];
+    const int tl = blockIdx.y;
+    const V* f = ptrs[t0 + tl];
+    V* w = W + (int64_t)tl * 4 * sites;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t s0 = (int64_t)blockIdx.x * kSitesPerBlock;
+    for (int k = 0; k < kSitesPerBlock / kThreads; ++k) {
+        const int64_t i = s0 + k * kThreads + threadIdx.x;
+        if (i >= sites) break;
+        const V p1 = f[i], p0 = f[sites + i], pm = f[2 * sites + i];
+        const double a1r = p1.x, a1i = p1.y, a0r = p0.x, a0i = p0.y, amr = pm.x, ami = pm.y;
+        const double n1 = a1r * a1r + a1i * a1i, n0 = a0r * a0r + a0i * a0i, nm = amr * amr + ami * ami;
+        const double rho = n1 + n0 + nm, fz = n1 - nm;
+        // F_perp = sqrt2 (conj(p1) p0 + conj(p0) pm)
+        const double s2 = 1.41421356237309504880;
+        const double fr = s2 * ((a1r * a0r + a1i * a0i) + (a0r * amr + a0i * ami));
+        const double fi = s2 * ((a1r * a0i - a1i * a0r) + (a0r * ami - a0i * amr));
+        acc[0] += n1;
+        acc[1] += n0;
+        acc[2] += nm;
+        acc[3] += q * (n1 + nm);
+        acc[4] += 0.5 * c0 * rho * rho;
+        acc[5] += 0.5 * c1 * (fz * fz + fr * fr + fi * fi);
+        w[i] = p1;
+        w[sites + i] = p0;
+        w[2 * sites + i] = pm;
+        w[3 * sites + i] = mk((T)fr, (T)fi);
+    }
+    block_sum<6>(acc, sm);
+    if (threadIdx.x == 0) {
+        double* o = part + ((int64_t)tl * nblk + blockIdx.x) * 6;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[k] = acc[k];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_obs_ekin(const cplx<T>* __restrict__ W, int64_t sites, int nx, int ny, int nz, double dx,
+           double* __restrict__ ekin, int64_t nblk) {
+    using V = cplx<T>;
+    __shared__ double sm[32];
+    const int tl = blockIdx.z, c = blockIdx.y;
+    const V* w = W + ((int64_t)tl * 4 + c) * sites;
+    const double two_pi = 6.283185307179586476925286766559;
+    const double gx = two_pi / (nx * dx), gy = two_pi / (ny * dx), gz = two_pi / (nz * dx);
+    double acc[1] = {0.0};
+    const int64_t s0 = (int64_t)blockIdx.x * kSitesPerBlock;
+    for (int k = 0; k < kSitesPerBlock / kThreads; ++k) {
+        const int64_t i = s0 + k * kThreads + threadIdx.x;
+        if (i >= sites) break;
+        const int ix = (int)(i % nx);
+        const int iy = (int)((i / nx) % ny);
+        const int iz = (int)(i / ((int64_t)nx * ny));
+        const int jx = ix < nx / 2 ? ix : ix - nx, jy = iy < ny / 2 ? iy : iy - ny, jz = iz < nz / 2 ? iz : iz - nz;
+        const double kx = gx * jx, ky = gy * jy, kz = gz * jz;
+        const V a = w[i];
+        const double p = (double)a.x * a.x + (double)a.y * a.y;
+        acc[0] += 0.5 * (kx * kx + ky * ky + kz * kz) * p;
+    }
+    block_sum<1>(acc, sm);
+    if (threadIdx.x == 0) ekin[((int64_t)tl * 3 + c) * nblk + blockIdx.x] = acc[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_obs_bins(const cplx<T>* __restrict__ W, int64_t sites, int ntl, const int32_t* __restrict__ off,
+           const int32_t* __restrict__ modes, double scale, double* __restrict__ acc_spec, int nbins) {
+    using V = cplx<T>;
+    __shared__ double sm[32];
+    const int b = blockIdx.x, qf = blockIdx.y;
+    const double sub = (qf < 3) ? 0.5 : 0.0;
+    const int beg = off[b], end = off[b + 1];
+    double acc[1] = {0.0};
+    for (int tl = 0; tl < ntl; ++tl) {
+        const V* w = W + ((int64_t)tl * 4 + qf) * sites;
+        for (int i = beg + threadIdx.x; i < end; i += kThreads) {
+            const V a = w[modes[i]];
+            acc[0] += ((double)a.x * a.x + (double)a.y * a.y) * scale - sub;
+        }
+    }
+    block_sum<1>(acc, sm);
+    if (threadIdx.x == 0) acc_spec[(int64_t)qf * nbins + b] += acc[0];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_obs_final(const double* __restrict__ part, const double* __restrict__ ekin, int64_t nblk, int64_t count,
+            const int32_t* __restrict__ ids, int t0, double vol, double inv_sites, double* __restrict__ acc_diag,
+            int* status) {
+    __shared__ double sm[7 * 32];
+    const int tl = blockIdx.x;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t k = threadIdx.x; k < count; k += kThreads) {
+        const double* p = part + ((int64_t)tl * nblk + k) * 6;
+        acc[0] += p[0];
+        acc[1] += p[1];
+        acc[2] += p[2];
+        acc[4] += p[3];
+        acc[5] += p[4];
+        acc[6] += p[5];
+        acc[3] += ekin[((int64_t)tl * 3 + 0) * nblk + k] + ekin[((int64_t)tl * 3 + 1) * nblk + k] +
+                  ekin[((int64_t)tl * 3 + 2) * nblk + k];
+    }
+    block_sum<7>(acc, sm);
+    if (threadIdx.x == 0) {
+        double* o = acc_diag + (int64_t)ids[t0 + tl] * 8;
+        bool finite = true;
+        for (int k = 0; k < 7; ++k) {
+            const double v = (k == 3) ? acc[k] * vol * inv_sites : acc[k] * vol;
+            finite = finite && isfinite(v);
+            o[k] += v;
+        }
+        if (!finite) atomicCAS(status, 0, (int)GPE_ENONFINITE);
+    }
+}
+
+template <typename T>
+gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q, double* acc, uint32_t flags,
+                     int slot, int* d_status, cudaStream_t s) {
+    using V = cplx<T>;
+    const int64_t slot_doubles = 4 * (int64_t)(w.nbins > 0 ? w.nbins : 0) + 8 * w.ntraj_total;
+    double* acc_slot = acc + (int64_t)slot * slot_doubles;
+    const int64_t nblk = (g.sites + kSitesPerBlock - 1) / kSitesPerBlock;
+    const double vol = std::pow(g.dx, g.ndim);
+    V* W = reinterpret_cast<V*>(w.d_W);
+    for (int t0 = 0; t0 < g.ntraj; t0 += (int)w.chunk) {
+        const int nc = (int)std::min<int64_t>(w.chunk, g.ntraj - t0);
+        k_obs_prep<T><<<dim3((unsigned)nblk, nc), kThreads, 0, s>>>(
+            reinterpret_cast<V* const*>(g.dptrs), t0, W, g.sites, c0, c1, q, w.d_part, w.nblk);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs prep", e);
+        const V* twx[3] = {reinterpret_cast<const V*>(g.tw[0][0]), reinterpret_cast<const V*>(g.tw[0][1]),
+                           reinterpret_cast<const V*>(g.tw[0][2])};
+        e = launch_rowfft<T>(g.n[0], W, (int64_t)nc * 4 * g.n[1] * g.n[2], twx, s);
+        if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs x fft", e);
+        for (int ax = 1; ax < g.ndim; ++ax) {
+            PassArgs<T> a{};
+            a.ptrs = reinterpret_cast<V* const*>(w.d_Wptrs);
+            a.comp_stride = g.sites;
+            a.ntraj = nc;
+            a.ncomp = 4;
+            for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const V*>(g.tw[ax][ri]);
+            const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+            if (ax == 1) {
+                a.stride = nx;
+                a.n_outer = nz;
+                a.outer_stride = (int64_t)nx * ny;
+            } else {
+                a.stride = (int64_t)nx * ny;
+                a.n_outer = ny;
+                a.outer_stride = nx;
+            }
+            a.nx_tiles = nx / colpass_cols<T>(g.n[ax]);
+            e = launch_colfft<T>(g.n[ax], a, s);
+            if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs strided fft", e);
+        }
+        if (flags & GPE_OBS_DIAG) {
+            k_obs_ekin<T><<<dim3((unsigned)nblk, 3, nc), kThreads, 0, s>>>(W, g.sites, g.n[0], g.n[1], g.n[2], g.dx,
+                                                                          w.d_ekin, w.nblk);
+            k_obs_final<<<nc, kThreads, 0, s>>>(w.d_part, w.d_ekin, w.nblk, nblk, g.d_ids, t0, vol, 1.0 / (double)g.sites,
+                                                acc_slot + 4 * (int64_t)(w.nbins > 0 ? w.nbins : 0), d_status);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs diagnostics", e);
+        }
+        if (flags & GPE_OBS_SPECTRA) {
+            k_obs_bins<T><<<dim3(w.nbins, 4), kThreads, 0, s>>>(W, g.sites, nc, w.d_off, w.d_modes,
+                                                               vol / (double)g.sites, acc_slot, w.nbins);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs bins", e);
+        }
+    }
+    return GPE_OK;
+}
+
+int64_t isqrt_round(int64_t m) {
+    // b with (2b - 1)^2 <= 4m < (2b + 1)^2
+    int64_t b = (int64_t)std::floor(std::sqrt((double)m) + 0.5);
+    while (b > 0 && (2 * b - 1) * (2 * b - 1) > 4 * m) --b;
+    while ((2 * b + 1) * (2 * b + 1) <= 4 * m) ++b;
+    return b;
+}
+
+}  // namespace
+
+const char* obs_last_error() { return g_obs_err.c_str(); }
+
+gpe_status obs_init(ObsWork& w, const std::vector<Group>& groups, bool f64, int) {
+    w.f64 = f64;
+    w.ntraj_total = 0;
+    for (const Group& g : groups) w.ntraj_total += g.ntraj;
+    w.nbins = 0;
+    if (groups.size() != 1) return GPE_OK;
+    const Group& g = groups[0];
+    for (int a = 1; a < g.ndim; ++a)
+        if (g.n[a] != g.n[0]) return GPE_OK;
+    const int n = g.n[0];
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    std::vector<int32_t> bin(g.sites);
+    int64_t maxb = 0;
+    for (int64_t i = 0; i < g.sites; ++i) {
+        const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((int64_t)nx * ny));
+        const int64_t jx = ix < nx / 2 ? ix : ix - nx, jy = iy < ny / 2 ? iy : iy - ny, jz = iz < nz / 2 ? iz : iz - nz;
+        const int64_t b = isqrt_round(jx * jx + jy * jy + jz * jz);
+        bin[i] = (int32_t)b;
+        if (b > maxb) maxb = b;
+    }
+    (void)n;
+    w.nbins = (int)(maxb + 1);
+    w.counts.assign(w.nbins, 0);
+    for (int64_t i = 0; i < g.sites; ++i) w.counts[bin[i]]++;
+    std::vector<int32_t> off(w.nbins + 1, 0), modes(g.sites);
+    for (int b = 0; b < w.nbins; ++b) off[b + 1] = off[b] + (int32_t)w.counts[b];
+    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    for (int64_t i = 0; i < g.sites; ++i) modes[fill[bin[i]]++] = (int32_t)i;
+    cudaError_t e = cudaMalloc(&w.d_off, sizeof(int32_t) * (w.nbins + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_modes, sizeof(int32_t) * g.sites);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return obs_fail(GPE_ENOMEM, "bin tables", e);
+    }
+    e = cudaMemcpy(w.d_off, off.data(), sizeof(int32_t) * (w.nbins + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(w.d_modes, modes.data(), sizeof(int32_t) * g.sites, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "copy bin tables", e);
+    return GPE_OK;
+}
+
+void obs_free(ObsWork& w) {
+    cudaFree(w.d_off);
+    cudaFree(w.d_modes);
+    cudaFree(w.d_W);
+    cudaFree(w.d_Wptrs);
+    cudaFree(w.d_part);
+    cudaFree(w.d_ekin);
+    w = ObsWork();
+}
+
+static gpe_status ensure_workspace(ObsWork& w, const std::vector<Group>& groups) {
+    if (w.ready) return GPE_OK;
+    const size_t vb = w.f64 ? 16 : 8;
+    int64_t max_sites = 0, max_traj = 0;
+    for (const Group& g : groups) {
+        max_sites = std::max(max_sites, g.sites);
+        max_traj = std::max<int64_t>(max_traj, g.ntraj);
+    }
+    const int64_t per_traj = 4 * max_sites * (int64_t)vb;
+    const int64_t budget = (int64_t)1 << 30;
+    w.chunk = std::max<int64_t>(1, std::min<int64_t>(max_traj, budget / per_traj));
+    w.nblk = (max_sites + kSitesPerBlock - 1) / kSitesPerBlock;
+    cudaError_t e = cudaMalloc(&w.d_W, (size_t)(w.chunk * per_traj));
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_Wptrs, sizeof(void*) * w.chunk);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_part, sizeof(double) * w.chunk * w.nblk * 6);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_ekin, sizeof(double) * w.chunk * w.nblk * 3);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return obs_fail(GPE_ENOMEM, "observables workspace", e);
+    }
+    std::vector<void*> ptrs(w.chunk);
+    for (int64_t i = 0; i < w.chunk; ++i) ptrs[i] = (char*)w.d_W + i * per_traj;
+    e = cudaMemcpy(w.d_Wptrs, ptrs.data(), sizeof(void*) * w.chunk, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "workspace pointers", e);
+    w.ready = true;
+    return GPE_OK;
+}
+
+gpe_status obs_accumulate(ObsWork& w, const std::vector<Group>& groups, bool f64, double c0, double c1, double q,
+                          double* acc, uint32_t flags, int slot, int* d_status, cudaStream_t s) {
+    gpe_status st = ensure_workspace(w, groups);
+    if (st != GPE_OK) return st;
+    for (const Group& g : groups) {
+        st = f64 ? run_group<double>(w, g, c0, c1, q, acc, flags, slot, d_status, s)
+                 : run_group<float>(w, g, c0, c1, q, acc, flags, slot, d_status, s);
+        if (st != GPE_OK) return st;
+    }
+    return GPE_OK;
+}
+
+}  // namespace gpe

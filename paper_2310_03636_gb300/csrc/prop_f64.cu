@@ -1,0 +1,61 @@
+// Row and column pass instantiations for double fields.
+#include "prop_kernels.cuh"
+
+namespace gpe {
+
+template <> int xpass_max_n<double>() { return 1024; }
+template <> int colpass_max_n<double>() { return 1024; }
+template <> int colpass_cols<double>(int n) { return Tune<double>::kColCols(n); }
+
+template <>
+cudaError_t launch_xpass<double>(int n, bool pre, const PassArgs<double>& a, cudaStream_t s) {
+    switch (n) {
+        case 64: return xpass_n<double, 64>(pre, a, s);
+        case 128: return xpass_n<double, 128>(pre, a, s);
+        case 256: return xpass_n<double, 256>(pre, a, s);
+        case 512: return xpass_n<double, 512>(pre, a, s);
+        case 1024: return xpass_n<double, 1024>(pre, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t launch_colpass<double>(int n, const PassArgs<double>& a, cudaStream_t s) {
+    switch (n) {
+        case 64: return colpass_n<double, 64, false>(a, s);
+        case 128: return colpass_n<double, 128, false>(a, s);
+        case 256: return colpass_n<double, 256, false>(a, s);
+        case 512: return colpass_n<double, 512, false>(a, s);
+        case 1024: return colpass_n<double, 1024, false>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t launch_colfft<double>(int n, const PassArgs<double>& a, cudaStream_t s) {
+    switch (n) {
+        case 64: return colpass_n<double, 64, true>(a, s);
+        case 128: return colpass_n<double, 128, true>(a, s);
+        case 256: return colpass_n<double, 256, true>(a, s);
+        case 512: return colpass_n<double, 512, true>(a, s);
+        case 1024: return colpass_n<double, 1024, true>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t launch_rowfft<double>(int n, cplx<double>* d, int64_t rows, const cplx<double>* const* tw, cudaStream_t s) {
+    switch (n) {
+        case 64: return rowfft_n<double, 64>(d, rows, tw, s);
+        case 128: return rowfft_n<double, 128>(d, rows, tw, s);
+        case 256: return rowfft_n<double, 256>(d, rows, tw, s);
+        case 512: return rowfft_n<double, 512>(d, rows, tw, s);
+        case 1024: return rowfft_n<double, 1024>(d, rows, tw, s);
+        case 2048: return rowfft_n<double, 2048>(d, rows, tw, s);
+        case 4096: return rowfft_n<double, 4096>(d, rows, tw, s);
+        case 8192: return rowfft_n<double, 8192>(d, rows, tw, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gpe

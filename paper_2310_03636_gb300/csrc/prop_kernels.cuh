@@ -1,0 +1,266 @@
+// Propagation kernels: the kinetic step as per-axis pencil passes (K is separable,
+// exp(-i tau |k|^2/2) = prod_a exp(-i tau k_a^2/2)), the x pass fused with the local
+// step, and a resident 1D kernel that keeps a whole trajectory on chip for all steps.
+#pragma once
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace gpe {
+
+// Shape choices per precision.
+template <typename T> struct Tune;
+template <> struct Tune<float> {
+    static constexpr int kXR = 8;        // points per thread, row pass (3 components live)
+    static constexpr int kColR = 16;     // points per thread, column pass
+    static constexpr int kColCols(int n) { return n >= 1024 ? 8 : 16; }
+    static constexpr int kResR(int n) { return n >= 1024 ? 16 : 8; }
+    static constexpr int kRowR(int n) { return n >= 256 ? 16 : 8; }
+};
+template <> struct Tune<double> {
+    static constexpr int kXR = 4;
+    static constexpr int kColR = 8;
+    static constexpr int kColCols(int) { return 8; }
+    static constexpr int kResR(int n) { return n >= 1024 ? 8 : 4; }
+    static constexpr int kRowR(int n) { return n >= 256 ? 8 : 4; }
+};
+
+template <int R> constexpr int tw_slot() { return R == 4 ? 0 : (R == 8 ? 1 : 2); }
+
+template <int N, int R> constexpr int rows_per_cta() { return (N / R) >= 256 ? 1 : 256 / (N / R); }
+
+// Row pass: for each x row of every trajectory (3 components together):
+//   [PRE: FFT_x, x ph_pre, iFFT_x]  [LOCAL: L(dt) per site]  FFT_x, x ph, iFFT_x.
+template <typename T, int N, int R, bool PRE, bool LOCAL>
+__global__ void __launch_bounds__(rows_per_cta<N, R>() * (N / R))
+k_xpass(const PassArgs<T> a) {
+    using V = cplx<T>;
+    constexpr int TP = N / R;
+    constexpr int RPC = rows_per_cta<N, R>();
+    constexpr int LD = smem_ld<T>(N);
+    constexpr int TWN = FftPlan<N, R>::tw_size();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    V* tws = sm + RPC * 3 * LD;
+    copy_table(tws, a.tw[tw_slot<R>()], TWN);
+    const int lrow = threadIdx.x / TP, t = threadIdx.x % TP;
+    const int64_t grow = (int64_t)blockIdx.x * RPC + lrow;
+    const bool valid = grow < a.total_rows;
+    const int64_t g = valid ? grow : 0;
+    const int traj = (int)(g / a.rows_per_traj);
+    const int64_t row = g - (int64_t)traj * a.rows_per_traj;
+    V* base = a.ptrs[traj] + row * N + t;
+    V* const buf[3] = {sm + (lrow * 3 + 0) * LD, sm + (lrow * 3 + 1) * LD, sm + (lrow * 3 + 2) * LD};
+    V v[3][R];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[c][m] = valid ? base[c * a.comp_stride + m * TP] : mk((T)0, (T)0);
+    __syncthreads();
+    if constexpr (PRE) {
+        fft_pencil<N, R, -1, 3, Sync::Block>(v, buf, tws, t);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const V f = a.ph_pre[t + m * TP];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[c][m] = cmul(v[c][m], f);
+        }
+        fft_pencil<N, R, +1, 3, Sync::Block>(v, buf, tws, t);
+    }
+    if constexpr (LOCAL) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) local_step<T>(v[0][m], v[1][m], v[2][m], a.coef);
+    }
+    fft_pencil<N, R, -1, 3, Sync::Block>(v, buf, tws, t);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        const V f = a.ph[t + m * TP];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c][m] = cmul(v[c][m], f);
+    }
+    fft_pencil<N, R, +1, 3, Sync::Block>(v, buf, tws, t);
+    if (valid) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int m = 0; m < R; ++m) base[c * a.comp_stride + m * TP] = v[c][m];
+    }
+}
+
+// Column pass: pencils of length N along a strided axis, COLS adjacent x columns per
+// block, one component: FFT, x ph, iFFT (FWD_ONLY: forward FFT only).
+// Block index -> (traj, comp, outer, x tile).
+template <typename T, int N, int R, int COLS, bool FWD_ONLY>
+__global__ void __launch_bounds__(COLS * (N / R))
+k_colpass(const PassArgs<T> a) {
+    using V = cplx<T>;
+    constexpr int TP = N / R;
+    constexpr int LD = smem_ld<T>(N);
+    constexpr int TWN = FftPlan<N, R>::tw_size();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    V* tws = sm + COLS * LD;
+    copy_table(tws, a.tw[tw_slot<R>()], TWN);
+    const int col = threadIdx.x % COLS, t = threadIdx.x / COLS;
+    int64_t tile = blockIdx.x;
+    const int xt = (int)(tile % a.nx_tiles);
+    tile /= a.nx_tiles;
+    const int o = (int)(tile % a.n_outer);
+    tile /= a.n_outer;
+    const int comp = (int)(tile % a.ncomp);
+    const int traj = (int)(tile / a.ncomp);
+    V* base = a.ptrs[traj] + comp * a.comp_stride + o * a.outer_stride + xt * COLS + col + t * a.stride;
+    V* const buf[1] = {sm + col * LD};
+    V v[1][R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[0][m] = base[(int64_t)m * TP * a.stride];
+    __syncthreads();
+    fft_pencil<N, R, -1, 1, Sync::Block>(v, buf, tws, t);
+    if constexpr (!FWD_ONLY) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[0][m] = cmul(v[0][m], a.ph[t + m * TP]);
+        fft_pencil<N, R, +1, 1, Sync::Block>(v, buf, tws, t);
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) base[(int64_t)m * TP * a.stride] = v[0][m];
+}
+
+// Forward FFT along x of independent rows (one component per row), in place.
+template <typename T, int N, int R>
+__global__ void __launch_bounds__(rows_per_cta<N, R>() * (N / R))
+k_rowfft(cplx<T>* __restrict__ data, int64_t rows, const cplx<T>* __restrict__ tw) {
+    using V = cplx<T>;
+    constexpr int TP = N / R;
+    constexpr int RPC = rows_per_cta<N, R>();
+    constexpr int LD = smem_ld<T>(N);
+    constexpr int TWN = FftPlan<N, R>::tw_size();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    V* tws = sm + RPC * LD;
+    copy_table(tws, tw, TWN);
+    const int lrow = threadIdx.x / TP, t = threadIdx.x % TP;
+    const int64_t grow = (int64_t)blockIdx.x * RPC + lrow;
+    const bool valid = grow < rows;
+    V* base = data + (valid ? grow : 0) * N + t;
+    V* const buf[1] = {sm + lrow * LD};
+    V v[1][R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[0][m] = valid ? base[m * TP] : mk((T)0, (T)0);
+    __syncthreads();
+    fft_pencil<N, R, -1, 1, Sync::Block>(v, buf, tws, t);
+    if (valid) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) base[m * TP] = v[0][m];
+    }
+}
+
+// Resident 1D: one block per trajectory, the field stays in registers (and the FFT
+// exchange buffers in shared memory) for all steps:
+//   K(dt/2) [L K(dt)]^(n-1) L K(dt/2).
+template <typename T, int N, int R>
+__global__ void __launch_bounds__(N / R)
+k_resident1d(const Res1DArgs<T> a) {
+    using V = cplx<T>;
+    constexpr int TP = N / R;
+    constexpr int LD = smem_ld<T>(N);
+    constexpr int TWN = FftPlan<N, R>::tw_size();
+    constexpr Sync SY = (TP <= 32) ? Sync::Warp : Sync::Block;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    V* tws = sm + 3 * LD;
+    copy_table(tws, a.tw[tw_slot<R>()], TWN);
+    const int t = threadIdx.x;
+    V* base = a.ptrs[blockIdx.x] + t;
+    V* const buf[3] = {sm, sm + LD, sm + 2 * LD};
+    V v[3][R];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[c][m] = base[c * N + m * TP];
+    __syncthreads();
+    fft_pencil<N, R, -1, 3, SY>(v, buf, tws, t);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        const V f = a.ph_half[t + m * TP];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c][m] = cmul(v[c][m], f);
+    }
+    fft_pencil<N, R, +1, 3, SY>(v, buf, tws, t);
+    LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt};
+    for (int64_t s = 0; s < a.nsteps; ++s) {
+        coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
+#pragma unroll
+        for (int m = 0; m < R; ++m) local_step<T>(v[0][m], v[1][m], v[2][m], coef);
+        fft_pencil<N, R, -1, 3, SY>(v, buf, tws, t);
+        const V* ph = (s == a.nsteps - 1) ? a.ph_half : a.ph_full;
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const V f = ph[t + m * TP];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[c][m] = cmul(v[c][m], f);
+        }
+        fft_pencil<N, R, +1, 3, SY>(v, buf, tws, t);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < R; ++m) base[c * N + m * TP] = v[c][m];
+}
+
+// ---------------------------------------------------------------- launch helpers
+
+template <typename K>
+inline cudaError_t launch_with_smem(K kernel, int grid, int block, size_t smem, cudaStream_t s,
+                                    const void* arg) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    void* args[] = {const_cast<void*>(arg)};
+    return cudaLaunchKernel((const void*)kernel, dim3(grid), dim3(block), args, smem, s);
+}
+
+template <typename T, int N>
+cudaError_t xpass_n(bool pre, const PassArgs<T>& a, cudaStream_t s) {
+    constexpr int R = Tune<T>::kXR;
+    constexpr int TP = N / R;
+    constexpr int RPC = rows_per_cta<N, R>();
+    const int64_t grid = (a.total_rows + RPC - 1) / RPC;
+    const size_t smem = ((size_t)RPC * 3 * smem_ld<T>(N) + FftPlan<N, R>::tw_size()) * sizeof(cplx<T>);
+    if (pre) return launch_with_smem(k_xpass<T, N, R, true, true>, (int)grid, RPC * TP, smem, s, &a);
+    return launch_with_smem(k_xpass<T, N, R, false, true>, (int)grid, RPC * TP, smem, s, &a);
+}
+
+template <typename T, int N, bool FWD_ONLY>
+cudaError_t colpass_n(const PassArgs<T>& a, cudaStream_t s) {
+    constexpr int R = Tune<T>::kColR;
+    constexpr int COLS = Tune<T>::kColCols(N);
+    const int64_t grid = (int64_t)a.ntraj * a.ncomp * a.n_outer * a.nx_tiles;
+    const size_t smem = ((size_t)COLS * smem_ld<T>(N) + FftPlan<N, R>::tw_size()) * sizeof(cplx<T>);
+    return launch_with_smem(k_colpass<T, N, R, COLS, FWD_ONLY>, (int)grid, COLS * (N / R), smem, s, &a);
+}
+
+template <typename T, int N>
+cudaError_t rowfft_n(cplx<T>* data, int64_t rows, const cplx<T>* const* tw, cudaStream_t s) {
+    constexpr int R = Tune<T>::kRowR(N);
+    constexpr int TP = N / R;
+    constexpr int RPC = rows_per_cta<N, R>();
+    const int64_t grid = (rows + RPC - 1) / RPC;
+    const size_t smem = ((size_t)RPC * smem_ld<T>(N) + FftPlan<N, R>::tw_size()) * sizeof(cplx<T>);
+    auto kern = k_rowfft<T, N, R>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<(int)grid, RPC * TP, smem, s>>>(data, rows, tw[tw_slot<R>()]);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t resident1d_n(const Res1DArgs<T>& a, cudaStream_t s) {
+    constexpr int R = Tune<T>::kResR(N);
+    const size_t smem = ((size_t)3 * smem_ld<T>(N) + FftPlan<N, R>::tw_size()) * sizeof(cplx<T>);
+    return launch_with_smem(k_resident1d<T, N, R>, a.ntraj, N / R, smem, s, &a);
+}
+
+}  // namespace gpe

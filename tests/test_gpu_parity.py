@@ -1,0 +1,303 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the same seeded
+inputs.  Tolerances: per-component relative L2 error <= 1e-11 (FP64 fields) and <= 1e-4
+(FP32 fields) after 200 steps; ensemble spectra within 1e-3 relative (FP32), 1e-10 (FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import gpe_oracle as O
+from oracle.philox import tw_noise
+from paper_2310_03636_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C0, C1, Q = 1.0, -0.1, 0.09
+MEAN = (0.0, 0.0, 1.0, 0.0, 0.0, 0.0)
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2310_03636_gb300 import binding
+    return binding
+
+
+def oracle_initial(shape, ntraj, seed, dx=1.0, npm=0.5, mean=MEAN, ids=None):
+    ids = range(ntraj) if ids is None else ids
+    out = []
+    for t in ids:
+        eta = tw_noise(shape, seed, t, npm, dx)
+        for m in range(3):
+            eta[m] += mean[2 * m] + 1j * mean[2 * m + 1]
+        out.append(eta)
+    return np.stack(out)
+
+
+def rel_l2_per_comp(gpu, ref):
+    """max over trajectories and components of ||gpu - ref|| / ||ref||."""
+    d = len(gpu.shape) - 2
+    ax = tuple(range(2, 2 + d))
+    num = np.sqrt((np.abs(gpu - ref) ** 2).sum(axis=ax))
+    den = np.sqrt((np.abs(ref) ** 2).sum(axis=ax))
+    return float((num / den).max())
+
+
+def run_oracle(psi0, dt, steps, d, c0=C0, c1=C1, q=Q, dx=1.0, t0=0.0):
+    return O.propagate(torch.as_tensor(psi0), dt, steps, c0, c1, q, dx, d, t0=t0).numpy()
+
+
+# ------------------------------------------------------------------ noise
+
+@pytest.mark.parametrize("dtype,shape,dx", [("c128", (64, 128), 1.0), ("c64", (256,), 0.5), ("c128", (64, 64, 64), 0.7)])
+def test_noise_matches_oracle(B, dtype, shape, dx):
+    b = B.GPEBatch(shape, 3, dtype, dx=dx)
+    mean = (0.1, -0.2, 0.9, 0.05, 0.0, 0.3)
+    b.init_noise(987654321012345, mean, 0.5)
+    gpu = b.psi.cpu().numpy()
+    ref = oracle_initial(shape, 3, 987654321012345, dx=dx, mean=mean)
+    tol = 1e-13 if dtype == "c128" else 2e-7
+    assert np.abs(gpu - ref).max() < tol * max(1.0, np.abs(ref).max())
+    b.close()
+
+
+# ------------------------------------------------------------------ propagation, FP64
+
+@pytest.mark.parametrize("shape,ntraj,dt,steps", [
+    ((256,), 1, 0.01, 200),          # 1D N = 256, one trajectory, dt = 0.01
+    ((64,), 3, 0.02, 150),
+    ((2048,), 2, 0.02, 60),
+    ((64, 128), 2, 0.02, 200),       # non-square 2D: transposed axes would fail
+    ((128, 64), 1, 0.02, 40),
+    ((64, 64, 128), 1, 0.02, 12),    # 3D with three distinct pass kinds
+])
+def test_propagation_fp64(B, shape, ntraj, dt, steps):
+    seed = 4242
+    b = B.GPEBatch(shape, ntraj, "c128", C0, C1, Q, dt)
+    b.init_noise(seed, MEAN, 0.5)
+    b.step(steps)
+    assert b.sync_status() == B.GPE_OK
+    gpu = b.psi.cpu().numpy()
+    ref = run_oracle(oracle_initial(shape, ntraj, seed), dt, steps, len(shape))
+    err = rel_l2_per_comp(gpu, ref)
+    assert err <= 1e-11, err
+    b.close()
+
+
+@pytest.mark.parametrize("shape,ntraj,steps", [((256,), 2, 200), ((128, 128), 4, 200), ((64, 64, 64), 1, 50)])
+def test_propagation_fp32(B, shape, ntraj, steps):
+    seed, dt = 77, 0.02
+    b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, dt)
+    b.init_noise(seed, MEAN, 0.5)
+    b.step(steps)
+    assert b.sync_status() == B.GPE_OK
+    gpu = b.psi.cpu().numpy().astype(np.complex128)
+    ref = run_oracle(oracle_initial(shape, ntraj, seed), dt, steps, len(shape))
+    err = rel_l2_per_comp(gpu, ref)
+    assert err <= 1e-4, err
+    b.close()
+
+
+def test_split_calls_and_time_dependent_q(B):
+    """q(t) ramp through knots, advanced in uneven chunks: same as the oracle's single run."""
+    shape, ntraj, dt, seed = (64, 64), 2, 0.02, 5
+    knots = np.linspace(0.2, 0.05, 7)
+    t_end = 60 * dt
+    b = B.GPEBatch(shape, ntraj, "c128", C0, C1, Q, dt, q_knots=knots, t_end=t_end)
+    b.init_noise(seed, MEAN, 0.5)
+    for n in (1, 17, 0, 30, 12):
+        b.step(n)
+    assert b.step_count == 60
+    gpu = b.psi.cpu().numpy()
+    qf = O.q_piecewise_linear(torch.as_tensor(knots), t_end)
+    ref = O.propagate(torch.as_tensor(oracle_initial(shape, ntraj, seed)), dt, 60, C0, C1, qf, 1.0, 2).numpy()
+    assert rel_l2_per_comp(gpu, ref) <= 1e-11
+    b.close()
+
+
+def test_1d_time_dependent_q(B):
+    shape, dt, seed = (512,), 0.01, 8
+    knots = [0.3, 0.0, 0.2]
+    b = B.GPEBatch(shape, 2, "c128", C0, C1, Q, dt, q_knots=knots, t_end=1.0)
+    b.init_noise(seed, MEAN, 0.5)
+    b.step(70)
+    b.step(50)
+    gpu = b.psi.cpu().numpy()
+    qf = O.q_piecewise_linear(torch.as_tensor(knots, dtype=torch.float64), 1.0)
+    ref = O.propagate(torch.as_tensor(oracle_initial(shape, 2, seed)), dt, 120, C0, C1, qf, 1.0, 1).numpy()
+    assert rel_l2_per_comp(gpu, ref) <= 1e-11
+    b.close()
+
+
+def test_smooth_field_dx_and_couplings(B):
+    """A caller-written initial field, dx != 1, other couplings (c1 > 0)."""
+    shape, dx, dt = (64, 128), 0.6, 0.015
+    psi0 = W.smooth_random_field(shape, 2, seed=19)
+    c0, c1, q = 0.7, 0.35, -0.05
+    psi = torch.as_tensor(psi0).to("cuda")
+    b = B.GPEBatch(shape, 2, "c128", c0, c1, q, dt, dx=dx, psi=psi.contiguous())
+    b.step(80)
+    ref = run_oracle(psi0, dt, 80, 2, c0, c1, q, dx)
+    assert rel_l2_per_comp(b.psi.cpu().numpy(), ref) <= 1e-11
+    b.close()
+
+
+def test_ragged_batch(B):
+    """Trajectories of different shapes in one batch, each matches the oracle."""
+    import ctypes
+    shapes = [(256,), (64, 64), (128,), (64, 64)]
+    b = B.GPEBatch(list(shapes), dtype="c128", dt=0.02)
+    b.init_noise(31, MEAN, 0.5)
+    b.step(40)
+    for i, s in enumerate(shapes):
+        ref = run_oracle(oracle_initial(s, 1, 31, ids=[i]), 0.02, 40, len(s))
+        assert rel_l2_per_comp(b.psi[i].cpu().numpy()[None], ref) <= 1e-11
+    nb, sd = b.layout()
+    assert nb == 0 and sd == 8 * 4
+    acc = torch.zeros(sd, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.GPEError) as ei:
+        b.observables(acc, B.GPE_OBS_SPECTRA, 0)
+    assert ei.value.status == B.GPE_EUNSUPPORTED
+    b.observables(acc, B.GPE_OBS_DIAG, 0)
+    diag = acc.cpu().numpy().reshape(4, 8)
+    for i, s in enumerate(shapes):
+        p = torch.as_tensor(b.psi[i].cpu().numpy())
+        ref = O.diagnostics(p, 1.0, C0, C1, Q, len(s)).numpy()
+        np.testing.assert_allclose(diag[i, :7], ref, rtol=1e-10, atol=1e-9)
+    b.close()
+
+
+# ------------------------------------------------------------------ observables
+
+def oracle_observables(psi, dx, d, q=Q):
+    """Spectra summed over trajectories per radial bin, and per-trajectory diagnostics."""
+    p = torch.as_tensor(psi)
+    shape = psi.shape[2:]
+    bins = O.radial_bins(shape)
+    nk = O.bin_sum(O.occupation_modes(p, dx, d), bins).sum(0).numpy()      # (3, nb)
+    sk = O.bin_sum(O.spin_structure_modes(p, dx, d), bins).sum(0).numpy()  # (nb,)
+    spec = np.concatenate([nk, sk[None]], 0)
+    diag = O.diagnostics(p, dx, C0, C1, q, d).numpy()
+    return spec, diag, O.bin_counts(shape).numpy()
+
+
+@pytest.mark.parametrize("dtype,shape,ntraj,dx,steps", [
+    ("c128", (256,), 1, 1.0, 100),
+    ("c128", (128, 128), 3, 0.8, 30),
+    ("c64", (128, 128), 4, 1.0, 30),
+    ("c128", (64, 64, 64), 2, 1.0, 5),
+])
+def test_observables(B, dtype, shape, ntraj, dx, steps):
+    b = B.GPEBatch(shape, ntraj, dtype, C0, C1, Q, 0.02, dx=dx)
+    b.init_noise(11, MEAN, 0.5)
+    b.step(steps)
+    nb, sd = b.layout()
+    acc = b.new_accumulator(3)
+    b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 1)
+    b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 1)     # accumulates: x2
+    assert b.sync_status() == B.GPE_OK
+    a = acc.cpu().numpy()
+    assert np.all(a[:sd] == 0) and np.all(a[2 * sd:] == 0)
+    spec, diag = B.unpack_slot(a[sd:2 * sd], nb, ntraj)
+    psi = b.psi.cpu().numpy().astype(np.complex128)
+    rs, rd, counts = oracle_observables(psi, dx, len(shape))
+    np.testing.assert_array_equal(b.bin_counts(), counts)
+    tol = 1e-10 if dtype == "c128" else 1e-5
+    scale = np.abs(rs).max(axis=1, keepdims=True)
+    assert np.abs(spec / 2 - rs).max() <= tol * scale.max()
+    np.testing.assert_allclose(diag[:, :7] / 2, rd, rtol=tol, atol=tol * np.abs(rd).max())
+    # deterministic: a second identical accumulation gives bitwise identical sums
+    acc2 = b.new_accumulator(3)
+    b.observables(acc2, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 1)
+    b.observables(acc2, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 1)
+    assert torch.equal(acc, acc2)
+    b.close()
+
+
+def test_spectra_fp32_vs_oracle_ensemble(B):
+    """FP32 fields, ensemble spectra within 1e-3 relative of the FP64 oracle run."""
+    shape, ntraj, steps, dt, seed = (128, 128), 8, 200, 0.02, 3
+    b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, dt)
+    b.init_noise(seed, MEAN, 0.5)
+    b.step(steps)
+    nb, sd = b.layout()
+    acc = b.new_accumulator(1)
+    b.observables(acc, B.GPE_OBS_SPECTRA, 0)
+    spec, _ = B.unpack_slot(acc, nb, ntraj)
+    ref_psi = run_oracle(oracle_initial(shape, ntraj, seed), dt, steps, 2)
+    rs, _, counts = oracle_observables(ref_psi, 1.0, 2)
+    # compare the bin means of S_perp and of |A_m|^2 (n_m + 1/2)
+    cnt = counts * ntraj
+    gS, rS = spec[3] / cnt, rs[3] / cnt
+    assert np.abs(gS - rS).max() / np.abs(rS).max() <= 1e-3
+    gN, rN = spec[:3] / cnt + 0.5, rs[:3] / cnt + 0.5
+    assert (np.abs(gN - rN) / np.abs(rN)).max() <= 1e-3
+    b.close()
+
+
+# ------------------------------------------------------------------ edge cases and errors
+
+def test_zero_steps_is_noop(B):
+    b = B.GPEBatch((64, 64), 1, "c64")
+    b.init_noise(1, MEAN, 0.5)
+    before = b.psi.clone()
+    b.step(0)
+    torch.cuda.synchronize()
+    assert torch.equal(before, b.psi)
+    b.close()
+
+
+def test_invalid_arguments(B):
+    psi = torch.zeros((3, 64, 64), dtype=torch.complex64, device="cuda")
+    with pytest.raises(B.GPEError) as e:
+        B.gpe_batch_create([((64, 60), 1.0, psi)], B.GPE_C64, 1, -0.1, 0.09, 0.02)
+    assert e.value.status == B.GPE_EINVAL
+    with pytest.raises(B.GPEError) as e:
+        B.gpe_batch_create([((64, 64), 1.0, psi)], B.GPE_C64, 1, -0.1, 0.09, -0.02)
+    assert e.value.status == B.GPE_EINVAL
+    big = torch.zeros((3, 2048, 64), dtype=torch.complex64, device="cuda")
+    with pytest.raises(B.GPEError) as e:
+        B.gpe_batch_create([((2048, 64), 1.0, big)], B.GPE_C64, 1, -0.1, 0.09, 0.02)
+    assert e.value.status == B.GPE_EUNSUPPORTED
+    b = B.GPEBatch((64, 64), 1, "c64")
+    with pytest.raises(B.GPEError) as e:
+        b.step(-1)
+    assert e.value.status == B.GPE_EINVAL
+    acc = b.new_accumulator(1)
+    with pytest.raises(B.GPEError) as e:
+        b.observables(acc, 0x10, 0)
+    assert e.value.status == B.GPE_EINVAL
+    b.close()
+
+
+def test_nonfinite_is_reported(B):
+    """A NaN in the field is caught by the FP64 diagnostics reduction (status word)."""
+    b = B.GPEBatch((64, 64), 1, "c64")
+    b.init_noise(2, MEAN, 0.5)
+    b.psi[0, 1, 3, 5] = float("nan")
+    acc = b.new_accumulator(1)
+    b.observables(acc, B.GPE_OBS_DIAG, 0)
+    assert b.sync_status() == B.GPE_ENONFINITE
+    assert b.sync_status() == B.GPE_OK      # cleared
+    b.close()
+
+
+# ------------------------------------------------------------------ full size, sampled
+
+def test_full_size_2d_512_sampled(B):
+    """The 2D 512^2 x 64-trajectory FP32 workload in the launch configuration the bench
+    times; sampled trajectories checked against the oracle after 60 steps."""
+    wl = W.C2_2D
+    b = B.GPEBatch(wl.shape, wl.ntraj, "c64", wl.c0, wl.c1, wl.q, wl.dt)
+    seed = W.SEED_BASE
+    b.init_noise(seed, wl.mean_spinor(), wl.noise_per_mode)
+    b.step(60)
+    assert b.sync_status() == B.GPE_OK
+    for t in (0, 37, 63):
+        gpu = b.psi[t:t + 1].cpu().numpy().astype(np.complex128)
+        ref = run_oracle(oracle_initial(wl.shape, 1, seed, ids=[t]), wl.dt, 60, 2)
+        assert rel_l2_per_comp(gpu, ref) <= 1e-4
+    b.close()
