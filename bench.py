@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput of the spin-1 GPE split-step hot path (site-updates/s).
+
+Workload: 2D 512^2 periodic grid, 64 truncated-Wigner trajectories per GPU, complex64
+fields with FP64 reductions, polar-state quench (c0 = 1, c1 = -0.1, q = 0.09), dt = 0.02,
+ensemble spectra n_m(k) and S_perp(k) plus diagnostics every 250 steps.  One bench step
+= one sampling interval: 250 time steps of the whole batch + one observables_accumulate.
+site-updates = points x 3 components x time steps x trajectories.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run, one rank per GPU; trajectories are sharded
+(each rank advances its own 64), the FP64 accumulators are summed across ranks once at
+the end (the path's only exchange step).  Rank 0 prints one JSON line.
+"""
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+from paper_2310_03636_gb300 import workloads as W  # noqa: E402
+
+STEPS_PER_SAMPLE = 250
+WL = W.C2_2D
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup(n):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2310_03636_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class):
+    """DRAM bytes per launch from the committed ncu summary, if the kernels are unchanged."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    v = d.get("per_launch_bytes", {}).get(kernel_class)
+    return float(v) if v is not None else None
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_sample(seconds_target=12.0):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: one 512^2 trajectory,
+    as many Strang steps as fit in about ``seconds_target`` seconds, plus its spectra."""
+    from oracle import gpe_oracle as O
+    from oracle.philox import tw_noise
+    psi = tw_noise(WL.shape, W.SEED_BASE, 0, WL.noise_per_mode, WL.dx)
+    psi[1] += math.sqrt(WL.n)
+    p = torch.as_tensor(psi)
+    t0 = time.perf_counter()
+    p = O.strang_step(p, WL.dt, WL.c0, WL.c1, WL.q, WL.dx, 2)
+    one = time.perf_counter() - t0
+    nsteps = max(1, int(seconds_target / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    p = O.propagate(p, WL.dt, nsteps, WL.c0, WL.c1, WL.q, WL.dx, 2)
+    bins = O.radial_bins(WL.shape)
+    O.bin_sum(O.occupation_modes(p, WL.dx, 2), bins)
+    O.bin_sum(O.spin_structure_modes(p, WL.dx, 2), bins)
+    el = time.perf_counter() - t0
+    su = WL.sites * 3 * nsteps
+    return {"value": su / el, "unit": "site-updates/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"1 trajectory of the 512^2 workload, {nsteps} steps + one spectra evaluation, "
+                      f"{el:.1f} s, FP64 torch CPU"}
+
+
+def run_reference(args):
+    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    per_step = max(2.0, 40.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(per_step)
+    vals = []
+    t0 = time.perf_counter()
+    samples = []
+    for _ in range(args.steps):
+        r = oracle_sample(per_step)
+        vals.append(r["value"])
+        samples.append(r["sample"])
+    el = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    out = {"impl": "reference", "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WL.name, "grid": list(WL.shape), "ntraj": 1, "dt": WL.dt},
+           "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": torch.get_num_threads(),
+                            "kind": "oracle", "sample": samples[0] if samples else ""},
+           "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    from paper_2310_03636_gb300 import binding as B
+    ws, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    seed = W.SEED_BASE + 1000003 * rank
+    b = B.GPEBatch(WL.shape, WL.ntraj, "c64", WL.c0, WL.c1, WL.q, WL.dt, dx=WL.dx)
+    nb, sd = b.layout()
+    nslots = args.warmup + args.steps
+    acc = torch.zeros(nslots * sd, dtype=torch.float64, device=dev)
+    b.init_noise(seed, WL.mean_spinor(), WL.noise_per_mode)
+    for k in range(args.warmup):
+        b.step(STEPS_PER_SAMPLE)
+        b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, k)
+    torch.cuda.synchronize()
+    assert b.sync_status() == B.GPE_OK
+
+    clocks = Clocks(dev.index)
+    su_per_step = WL.site_updates_per_step * STEPS_PER_SAMPLE
+    B.gpe_profile_enable(b.h, True)
+    B.gpe_profile_read(b.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    l0 = B.gpe_launch_count()
+    e0.record(stream)
+    for k in range(args.steps):
+        b.step(STEPS_PER_SAMPLE)
+        b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, args.warmup + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = B.gpe_launch_count() - l0
+    barrier(ws)
+    clk = clocks.stop()
+    prof = B.gpe_profile_read(b.h)
+    B.gpe_profile_enable(b.h, False)
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, ws)
+    status = b.sync_status()
+    value = su_per_step * args.steps * ws / (ms * 1e-3)
+
+    # ensemble exchange: sum the FP64 accumulators over ranks
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(acc, op=dist.ReduceOp.SUM)
+
+    # roofline of the dominant kernel class (bytes per launch: read + write of the 3-component field)
+    peak, peak_kind = measured_peaks()
+    dom = max(("xpass", "strided_pass"), key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    bytes_per_launch = 16.0 * WL.sites * 3 * WL.ntraj
+    achieved = bytes_per_launch / (dom_ms / dom_n * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(dom), "kernel": dom, "peak_source": peak_kind,
+                "avg_launch_us": dom_ms / dom_n * 1e3,
+                "classes_ms": {k: v[0] for k, v in prof.items() if v[1]},
+                "classes_launches": {k: v[1] for k, v in prof.items() if v[1]},
+                "effective_frac_16B_per_su": value / ws * 16.0 / (peak * 1e9)}
+
+    # end to end through the API with host buffers: H2D of the initial fields from pinned
+    # memory, the sampling interval, D2H of the accumulator slot
+    host_psi = torch.empty_like(b.psi, device="cpu").pin_memory()
+    host_psi.copy_(b.psi)
+    host_acc = torch.empty(sd, dtype=torch.float64).pin_memory()
+    k_e2e = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    barrier(ws)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    f0.record(stream)
+    for k in range(k_e2e):
+        b.psi.copy_(host_psi, non_blocking=True)
+        b.step(STEPS_PER_SAMPLE)
+        b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 0)
+        host_acc.copy_(acc[:sd], non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), ws)
+    e2e = {"value": su_per_step * k_e2e * ws / (e2e_ms * 1e-3), "unit": "site-updates/s",
+           "h2d_bytes_per_step": int(b.psi.numel() * b.psi.element_size()),
+           "d2h_bytes_per_step": int(sd * 8), "steps": k_e2e}
+    b.close()
+
+    # plain FP64 comparator: one trajectory per launch, no graph
+    fp64 = None
+    if rank == 0:
+        pb = B.GPEBatch(WL.shape, 1, "c128", WL.c0, WL.c1, WL.q, WL.dt, dx=WL.dx)
+        pb.init_noise(seed, WL.mean_spinor(), WL.noise_per_mode)
+        pb.step(5)
+        torch.cuda.synchronize()
+        n64 = 40
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        pb.step(n64)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        v64 = WL.sites * 3 * n64 / (g0.elapsed_time(g1) * 1e-3)
+        fp64 = {"value": v64, "unit": "site-updates/s", "ms_per_step": g0.elapsed_time(g1) / n64,
+                "what": "complex128 fields, FP64 arithmetic, one 512^2 trajectory per launch, no graph",
+                "fp32_batched_speedup": value / ws / v64}
+        pb.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+
+    if rank == 0:
+        out = {"metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": WL.name, "grid": list(WL.shape), "ntraj_per_gpu": WL.ntraj,
+                          "dt": WL.dt, "steps_per_bench_step": STEPS_PER_SAMPLE,
+                          "observables_every": STEPS_PER_SAMPLE, "c0": WL.c0, "c1": WL.c1, "q": WL.q,
+                          "parallelism": f"trajectories sharded over {ws} GPU(s)",
+                          "l2": "inputs larger than L2 (403 MB of fields per GPU)"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "gpu_launches": launches, "fp64_plain": fp64, "status": status}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

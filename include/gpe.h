@@ -47,7 +47,7 @@ typedef enum {
 typedef enum { GPE_C64 = 0, GPE_C128 = 1 } gpe_dtype;
 
 /* One trajectory.  ndim in {1,2,3}; n[a] = points along axis a (x = 0), each a power
- * of two in [64, 1024] for ndim >= 2 and in [64, 8192] (C64) / [64, 4096] (C128) for
+ * of two in [64, 1024] for ndim >= 2 and in [64, 4096] (C64) / [64, 2048] (C128) for
  * ndim = 1; unused axes must be 1.  dx = lattice spacing (all axes).  psi = device
  * pointer to the [3][n2][n1][n0] field (caller-owned, 16-byte aligned). */
 typedef struct {
@@ -112,7 +112,9 @@ gpe_status gpe_step_batch(gpe_batch* batch, int64_t nsteps, void* stream);
  * with bin b = round(|k| / (2 pi / L)); then [ntraj][8] diagnostics (N_1, N_0, N_-1,
  * E_kin, E_q, E_c0, E_c1, 0), E = dx^d sum_x [psi^*(-Laplacian/2)psi + q (n_1 + n_-1)
  * + c0 rho^2 / 2 + c1 (F_z^2 + |F_perp|^2) / 2] at the current q.  Sums are
- * deterministic (fixed reduction order).  The fields are not modified.
+ * deterministic (fixed reduction order).  The fields are not modified.  The first call
+ * on a batch allocates the handle's spectra workspace (four fields per trajectory, in
+ * chunks of at most 1 GiB); make it before capturing a stream.
  * Errors: GPE_EINVAL (NULL acc, sample_slot < 0, unknown flags), GPE_EUNSUPPORTED
  * (spectra requested for a batch with more than one shape or unequal sides). */
 gpe_status observables_accumulate(gpe_batch* batch, double* acc, uint32_t flags,
@@ -128,6 +130,18 @@ gpe_status gpe_bin_counts(const gpe_batch* batch, int64_t* counts);
 /* Batch time as a step count (t = step * dt); settable for replaying segments. */
 int64_t gpe_batch_get_step(const gpe_batch* batch);
 gpe_status gpe_batch_set_step(gpe_batch* batch, int64_t step);
+
+/* Measurement: when enabled, every launch the batch makes is bracketed by CUDA events on
+ * its stream, summed per kernel class: 0 = x pass (local step fused with the x kinetic
+ * pass), 1 = strided kinetic pass (y or z), 2 = resident 1D kernel, 3 = noise,
+ * 4 = observables (whole pipeline of one call).  gpe_profile_read synchronises the
+ * device, writes the summed milliseconds and launch counts of each class (arrays of 5,
+ * host) since the last read, and resets them. */
+gpe_status gpe_profile_enable(gpe_batch* batch, int32_t enable);
+gpe_status gpe_profile_read(gpe_batch* batch, double* ms, int64_t* launches);
+
+/* Number of kernels this library has launched since it was loaded (all batches). */
+int64_t gpe_launch_count(void);
 
 /* Synchronises ``stream`` and returns the device status word (GPE_OK if clean) and
  * clears it. */

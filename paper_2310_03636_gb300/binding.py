@@ -55,6 +55,9 @@ def _load():
         "gpe_batch_get_step": ([vp], i64),
         "gpe_batch_set_step": ([vp, i64], ctypes.c_int),
         "gpe_sync_status": ([vp, vp], ctypes.c_int),
+        "gpe_profile_enable": ([vp, i32], ctypes.c_int),
+        "gpe_profile_read": ([vp, pd, ctypes.POINTER(i64)], ctypes.c_int),
+        "gpe_launch_count": ([], i64),
         "gpe_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -135,6 +138,24 @@ def gpe_bin_counts(h, nbins):
 
 def gpe_sync_status(h, stream=None):
     return LIB.gpe_sync_status(h, _stream(stream))
+
+
+PROFILE_KINDS = ("xpass", "strided_pass", "resident1d", "noise", "observables")
+
+
+def gpe_profile_enable(h, on=True):
+    _check(LIB.gpe_profile_enable(h, 1 if on else 0))
+
+
+def gpe_profile_read(h):
+    ms = (ctypes.c_double * 5)()
+    n = (ctypes.c_int64 * 5)()
+    _check(LIB.gpe_profile_read(h, ms, n))
+    return {k: (ms[i], n[i]) for i, k in enumerate(PROFILE_KINDS)}
+
+
+def gpe_launch_count():
+    return LIB.gpe_launch_count()
 
 
 # ----------------------------------------------------------------- convenience

@@ -11,6 +11,14 @@ template <> struct cplx_sel<float> { using type = float2; };
 template <> struct cplx_sel<double> { using type = double2; };
 template <typename T> using cplx = typename cplx_sel<T>::type;
 
+// Table entry for twiddles and phase factors: FP32 tables carry each constant as a
+// hi + lo pair (hi = fl(c), lo = fl(c - hi)), so the rounding of the constant itself,
+// which would repeat identically in every step, drops to O(eps^2); FP64 tables hold c.
+template <typename T> struct tw_sel;
+template <> struct tw_sel<float> { using type = float4; };
+template <> struct tw_sel<double> { using type = double2; };
+template <typename T> using twel = typename tw_sel<T>::type;
+
 __host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 __host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
 
@@ -29,6 +37,27 @@ template <typename V, typename T> __device__ __forceinline__ V cscale(V a, T s) 
 // -i * a
 template <typename V> __device__ __forceinline__ V cmul_mi(V a) { return mk(a.y, -a.x); }
 template <typename V> __device__ __forceinline__ auto cabs2(V a) { return a.x * a.x + a.y * a.y; }
+
+// w * f (DIR < 0) or w * conj(f) (DIR > 0) with f a table entry.
+template <int DIR>
+__device__ __forceinline__ float2 twmul(float2 w, float4 f) {
+    const float fy = DIR < 0 ? f.y : -f.y, ly = DIR < 0 ? f.w : -f.w;
+    const float sr = fmaf(w.x, f.z, -w.y * ly);
+    const float si = fmaf(w.x, ly, w.y * f.z);
+    return mk(fmaf(w.x, f.x, fmaf(-w.y, fy, sr)), fmaf(w.x, fy, fmaf(w.y, f.x, si)));
+}
+template <int DIR>
+__device__ __forceinline__ double2 twmul(double2 w, double2 f) {
+    const double fy = DIR < 0 ? f.y : -f.y;
+    return mk(w.x * f.x - w.y * fy, w.x * fy + w.y * f.x);
+}
+// x * c for a compile-time constant c given in double: FP32 uses c_hi + c_lo.
+__device__ __forceinline__ float mulc(float x, double c) {
+    const float hi = (float)c;
+    const float lo = (float)(c - (double)hi);
+    return fmaf(x, lo, x * hi);
+}
+__device__ __forceinline__ double mulc(double x, double c) { return x * c; }
 
 __device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }

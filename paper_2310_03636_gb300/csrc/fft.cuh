@@ -9,8 +9,10 @@
 // first stage of the inverse transform needs, so a momentum-space phase multiply sits
 // between them without a shared-memory round trip.
 //
-// Twiddle factors W_N^i = exp(-2 pi i i / N) come from a table computed in FP64 and
-// rounded once to T.  Transforms are unnormalised (the 1/N goes into the phase table).
+// Twiddle factors come from tables computed in FP64; FP32 tables hold hi + lo pairs so
+// that the constants carry no O(eps) bias (their rounding error would otherwise repeat
+// identically in every time step and accumulate linearly).  Transforms are unnormalised
+// (the 1/N goes into the phase table).
 #pragma once
 
 #include "common.cuh"
@@ -49,13 +51,12 @@ __device__ __forceinline__ V twc16(V a, int e) {
     const double cr = cos16(e);
     const double ci = DIR * cos16(e + 12);
     if ((e & 1) == 0) {
-        const T h = (T)0.70710678118654752440;
+        const double h = 0.70710678118654752440;
         const T xr = cr > 0 ? a.x : -a.x, yr = cr > 0 ? a.y : -a.y;
         const T xi = ci > 0 ? a.x : -a.x, yi = ci > 0 ? a.y : -a.y;
-        return mk(h * (xr - yi), h * (xi + yr));
+        return mk(mulc(xr - yi, h), mulc(xi + yr, h));
     }
-    const T c = (T)cr, s = (T)ci;
-    return mk(a.x * c - a.y * s, a.x * s + a.y * c);
+    return mk(mulc(a.x, cr) - mulc(a.y, ci), mulc(a.x, ci) + mulc(a.y, cr));
 }
 
 // In-register DFT of size R on v[0], v[S], ..., v[(R-1) S]; natural order in and out.
@@ -153,9 +154,9 @@ struct FftPlan {
 };
 
 // One Stockham stage S of radix RS on sub-transforms of length NS.
-template <int N, int R, int DIR, int NC, int S, Sync SY, typename V>
+template <int N, int R, int DIR, int NC, int S, Sync SY, typename V, typename TW>
 __device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC],
-                                               const V* __restrict__ tws, int t) {
+                                               const TW* __restrict__ tws, int t) {
     using P = FftPlan<N, R>;
     constexpr int TP = N / R;
     constexpr int RS = P::radix(S);
@@ -175,10 +176,9 @@ __device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < RS; ++r) {
-                V f = tws[OFF + (r - 1) * NS + k];
-                if (DIR > 0) f = cconj(f);
+                const TW f = tws[OFF + (r - 1) * NS + k];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) w[c][r] = cmul(w[c][r], f);
+                for (int c = 0; c < NC; ++c) w[c][r] = twmul<DIR>(w[c][r], f);
             }
         }
 #pragma unroll
@@ -206,9 +206,9 @@ __device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC
     }
 }
 
-template <int N, int R, int DIR, int NC, int S, Sync SY, typename V>
+template <int N, int R, int DIR, int NC, int S, Sync SY, typename V, typename TW>
 __device__ __forceinline__ void stockham_from(V (&v)[NC][R], V* const (&buf)[NC],
-                                              const V* __restrict__ tws, int t) {
+                                              const TW* __restrict__ tws, int t) {
     if constexpr (S < FftPlan<N, R>::kStages) {
         stockham_stage<N, R, DIR, NC, S, SY>(v, buf, tws, t);
         stockham_from<N, R, DIR, NC, S + 1, SY>(v, buf, tws, t);
@@ -219,9 +219,9 @@ __device__ __forceinline__ void stockham_from(V (&v)[NC][R], V* const (&buf)[NC]
 // (e^{-2 pi i jk/N}), +1 inverse (unnormalised).  Every thread of the sync group must
 // call it.  buf[c]: shared buffer of pencil c (smem_ld<T>(N) elements); tws: the stage
 // twiddle table of FftPlan<N, R> (usually a shared-memory copy).
-template <int N, int R, int DIR, int NC, Sync SY, typename V>
+template <int N, int R, int DIR, int NC, Sync SY, typename V, typename TW>
 __device__ __forceinline__ void fft_pencil(V (&v)[NC][R], V* const (&buf)[NC],
-                                           const V* __restrict__ tws, int t) {
+                                           const TW* __restrict__ tws, int t) {
     static_assert((N & (N - 1)) == 0 && N >= R, "N must be a power of two >= R");
     stockham_from<N, R, DIR, NC, 0, SY>(v, buf, tws, t);
 }

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <new>
 #include <string>
@@ -38,6 +39,25 @@ gpe_status fail(gpe_status s, const char* fmt, ...) {
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+std::atomic<int64_t> g_launches{0};
+
+constexpr int kProfKinds = 5;
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> open;
+    size_t used = 0;
+    cudaEvent_t get() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+};
+
 }  // namespace
 
 struct gpe_batch {
@@ -52,13 +72,46 @@ struct gpe_batch {
     int device = 0;
     std::vector<void*> allocs;
     ObsWork obs;
+    Profiler prof;
 };
 
 namespace {
 
+// Brackets one launch (or launch sequence) of class ``kind`` with events when profiling.
+struct ProfScope {
+    gpe_batch* b;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t e1 = nullptr;
+    ProfScope(gpe_batch* b_, int kind_, cudaStream_t s_, int64_t nlaunch) : b(b_), kind(kind_), s(s_) {
+        g_launches += nlaunch;
+        if (b->prof.on) {
+            cudaEvent_t e0 = b->prof.get();
+            e1 = b->prof.get();
+            cudaEventRecord(e0, s);
+            b->prof.open.push_back({kind, {e0, e1}});
+        }
+    }
+    ~ProfScope() {
+        if (e1) cudaEventRecord(e1, s);
+    }
+};
+
+}  // namespace
+
+namespace {
+
 // Kinetic phase tables exp(-i tau k^2/2) / n for tau = dt and dt/2, computed in FP64.
+// Table entry from an FP64 complex value: FP32 keeps hi = fl(c) and lo = fl(c - hi).
+template <typename T> twel<T> tw_entry(double re, double im);
+template <> float4 tw_entry<float>(double re, double im) {
+    const float hr = (float)re, hi = (float)im;
+    return make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+}
+template <> double2 tw_entry<double>(double re, double im) { return make_double2(re, im); }
+
 template <typename T>
-void phase_tables_host(int n, double dx, double dt, std::vector<cplx<T>>& pf, std::vector<cplx<T>>& ph) {
+void phase_tables_host(int n, double dx, double dt, std::vector<twel<T>>& pf, std::vector<twel<T>>& ph) {
     pf.resize(n);
     ph.resize(n);
     const double two_pi = 6.283185307179586476925286766559;
@@ -66,8 +119,8 @@ void phase_tables_host(int n, double dx, double dt, std::vector<cplx<T>>& pf, st
         const int j = (i < n / 2) ? i : i - n;
         const double k = two_pi * (double)j / ((double)n * dx);
         const double a_full = 0.5 * dt * k * k, a_half = 0.25 * dt * k * k;
-        pf[i] = mk((T)(std::cos(a_full) / n), (T)(-std::sin(a_full) / n));
-        ph[i] = mk((T)(std::cos(a_half) / n), (T)(-std::sin(a_half) / n));
+        pf[i] = tw_entry<T>(std::cos(a_full) / n, -std::sin(a_full) / n);
+        ph[i] = tw_entry<T>(std::cos(a_half) / n, -std::sin(a_half) / n);
     }
 }
 
@@ -75,14 +128,14 @@ void phase_tables_host(int n, double dx, double dt, std::vector<cplx<T>>& pf, st
 // device-side FftPlan<n, R> expects: for each stage with sub-length ns > 1 and radix rs,
 // a block [r = 1..rs-1][k = 0..ns-1] of exp(-2 pi i r k / (ns rs)), computed in FP64.
 template <typename T>
-std::vector<cplx<T>> stage_twiddles_host(int n, int R) {
+std::vector<twel<T>> stage_twiddles_host(int n, int R) {
     int logn = 0, logr = 0;
     while ((1 << logn) < n) ++logn;
     while ((1 << logr) < R) ++logr;
     const int nfull = logn / logr;
     const int last = 1 << (logn - nfull * logr);
     const int stages = nfull + (last > 1 ? 1 : 0);
-    std::vector<cplx<T>> out;
+    std::vector<twel<T>> out;
     const double two_pi = 6.283185307179586476925286766559;
     int ns = 1;
     for (int s = 0; s < stages; ++s) {
@@ -91,11 +144,11 @@ std::vector<cplx<T>> stage_twiddles_host(int n, int R) {
             for (int r = 1; r < rs; ++r)
                 for (int k = 0; k < ns; ++k) {
                     const double ang = two_pi * (double)r * (double)k / ((double)ns * rs);
-                    out.push_back(mk((T)std::cos(ang), (T)(-std::sin(ang))));
+                    out.push_back(tw_entry<T>(std::cos(ang), -std::sin(ang)));
                 }
         ns *= rs;
     }
-    if (out.empty()) out.push_back(mk((T)1, (T)0));
+    if (out.empty()) out.push_back(tw_entry<T>(1.0, 0.0));
     return out;
 }
 
@@ -112,17 +165,17 @@ gpe_status dev_alloc(gpe_batch* b, void** p, size_t bytes) {
 template <typename T>
 gpe_status build_group_tables(gpe_batch* b, Group& g) {
     for (int a = 0; a < g.ndim; ++a) {
-        std::vector<cplx<T>> pf, ph;
+        std::vector<twel<T>> pf, ph;
         phase_tables_host<T>(g.n[a], g.dx, b->p.dt, pf, ph);
-        const size_t bytes = sizeof(cplx<T>) * g.n[a];
+        const size_t bytes = sizeof(twel<T>) * g.n[a];
         gpe_status s;
         if ((s = dev_alloc(b, &g.ph_full[a], bytes)) != GPE_OK) return s;
         if ((s = dev_alloc(b, &g.ph_half[a], bytes)) != GPE_OK) return s;
         GPE_CK(cudaMemcpy(g.ph_full[a], pf.data(), bytes, cudaMemcpyHostToDevice));
         GPE_CK(cudaMemcpy(g.ph_half[a], ph.data(), bytes, cudaMemcpyHostToDevice));
         for (int ri = 0; ri < 3; ++ri) {
-            const std::vector<cplx<T>> tw = stage_twiddles_host<T>(g.n[a], 4 << ri);
-            const size_t tb = sizeof(cplx<T>) * tw.size();
+            const std::vector<twel<T>> tw = stage_twiddles_host<T>(g.n[a], 4 << ri);
+            const size_t tb = sizeof(twel<T>) * tw.size();
             if ((s = dev_alloc(b, &g.tw[a][ri], tb)) != GPE_OK) return s;
             GPE_CK(cudaMemcpy(g.tw[a][ri], tw.data(), tb, cudaMemcpyHostToDevice));
         }
@@ -173,10 +226,11 @@ PassArgs<T> base_args(const gpe_batch* b, const Group& g) {
 
 // Pure kinetic pass along axis ax (1 = y, 2 = z) with the full or half time step.
 template <typename T>
-cudaError_t col_pass(const gpe_batch* b, const Group& g, int ax, bool half, cudaStream_t s) {
+cudaError_t col_pass(gpe_batch* b, const Group& g, int ax, bool half, cudaStream_t s) {
+    ProfScope ps(b, 1, s, 1);
     PassArgs<T> a = base_args<T>(b, g);
-    for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const cplx<T>*>(g.tw[ax][ri]);
-    a.ph = reinterpret_cast<const cplx<T>*>(half ? g.ph_half[ax] : g.ph_full[ax]);
+    for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[ax][ri]);
+    a.ph = reinterpret_cast<const twel<T>*>(half ? g.ph_half[ax] : g.ph_full[ax]);
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (ax == 1) {
         a.stride = nx;
@@ -192,11 +246,12 @@ cudaError_t col_pass(const gpe_batch* b, const Group& g, int ax, bool half, cuda
 }
 
 template <typename T>
-cudaError_t x_pass(const gpe_batch* b, const Group& g, bool pre, bool half_post, double q, cudaStream_t s) {
+cudaError_t x_pass(gpe_batch* b, const Group& g, bool pre, bool half_post, double q, cudaStream_t s) {
+    ProfScope ps(b, 0, s, 1);
     PassArgs<T> a = base_args<T>(b, g);
-    for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const cplx<T>*>(g.tw[0][ri]);
-    a.ph_pre = reinterpret_cast<const cplx<T>*>(g.ph_half[0]);
-    a.ph = reinterpret_cast<const cplx<T>*>(half_post ? g.ph_half[0] : g.ph_full[0]);
+    for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[0][ri]);
+    a.ph_pre = reinterpret_cast<const twel<T>*>(g.ph_half[0]);
+    a.ph = reinterpret_cast<const twel<T>*>(half_post ? g.ph_half[0] : g.ph_full[0]);
     a.rows_per_traj = (int64_t)g.n[1] * g.n[2];
     a.total_rows = a.rows_per_traj * g.ntraj;
     a.coef.q = (T)q;
@@ -211,9 +266,9 @@ gpe_status step_group(gpe_batch* b, const Group& g, int64_t nsteps, cudaStream_t
         Res1DArgs<T> a{};
         a.ptrs = reinterpret_cast<cplx<T>* const*>(g.dptrs);
         a.ntraj = g.ntraj;
-        for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const cplx<T>*>(g.tw[0][ri]);
-        a.ph_full = reinterpret_cast<const cplx<T>*>(g.ph_full[0]);
-        a.ph_half = reinterpret_cast<const cplx<T>*>(g.ph_half[0]);
+        for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[0][ri]);
+        a.ph_full = reinterpret_cast<const twel<T>*>(g.ph_full[0]);
+        a.ph_half = reinterpret_cast<const twel<T>*>(g.ph_half[0]);
         a.c0 = (T)b->p.c0;
         a.c1 = (T)b->p.c1;
         a.dt = (T)dt;
@@ -224,6 +279,7 @@ gpe_status step_group(gpe_batch* b, const Group& g, int64_t nsteps, cudaStream_t
         a.knots = b->d_knots;
         a.n_knots = b->p.n_knots;
         a.nsteps = nsteps;
+        ProfScope ps(b, 2, s, 1);
         GPE_CK(launch_resident1d<T>(g.n[0], a, s));
         return GPE_OK;
     }
@@ -337,6 +393,7 @@ gpe_status gpe_batch_destroy(gpe_batch* b) {
     if (!b) return GPE_OK;
     cudaDeviceSynchronize();
     obs_free(b->obs);
+    for (cudaEvent_t e : b->prof.pool) cudaEventDestroy(e);
     for (void* p : b->allocs) cudaFree(p);
     delete b;
     return GPE_OK;
@@ -361,6 +418,7 @@ gpe_status tw_init_noise(gpe_batch* b, uint64_t seed, const double mean_spinor[6
         a.key1 = (uint32_t)(seed >> 32);
         a.sigma = std::sqrt(noise_per_mode / std::pow(g.dx, g.ndim));
         for (int i = 0; i < 6; ++i) a.mean[i] = mean_spinor[i];
+        ProfScope ps(b, 3, s, 1);
         GPE_CK(b->dtype == GPE_C64 ? launch_noise<float>(a, s) : launch_noise<double>(a, s));
     }
     b->step = 0;
@@ -390,6 +448,7 @@ gpe_status observables_accumulate(gpe_batch* b, double* acc, uint32_t flags, int
     if ((flags & GPE_OBS_SPECTRA) && b->obs.nbins <= 0)
         return fail(GPE_EUNSUPPORTED, "spectra need one shape with equal side lengths");
     const double q = q_at_host(b, (double)b->step * b->p.dt);
+    ProfScope ps(b, 4, (cudaStream_t)stream, obs_launches(b->obs, b->groups, flags));
     gpe_status s = obs_accumulate(b->obs, b->groups, b->dtype == GPE_C128, b->p.c0, b->p.c1, q, acc, flags, slot,
                                   b->d_status, (cudaStream_t)stream);
     if (s != GPE_OK) g_err = obs_last_error();
@@ -417,6 +476,32 @@ gpe_status gpe_batch_set_step(gpe_batch* b, int64_t step) {
     b->step = step;
     return GPE_OK;
 }
+
+gpe_status gpe_profile_enable(gpe_batch* b, int32_t enable) {
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    b->prof.on = enable != 0;
+    return GPE_OK;
+}
+
+gpe_status gpe_profile_read(gpe_batch* b, double* ms, int64_t* launches) {
+    if (!b || !ms || !launches) return fail(GPE_EINVAL, "NULL argument");
+    GPE_CK(cudaDeviceSynchronize());
+    for (int k = 0; k < kProfKinds; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (auto& o : b->prof.open) {
+        float t = 0.f;
+        GPE_CK(cudaEventElapsedTime(&t, o.second.first, o.second.second));
+        ms[o.first] += t;
+        launches[o.first] += 1;
+    }
+    b->prof.open.clear();
+    b->prof.used = 0;
+    return GPE_OK;
+}
+
+int64_t gpe_launch_count(void) { return g_launches.load(); }
 
 gpe_status gpe_sync_status(gpe_batch* b, void* stream) {
     g_err.clear();

@@ -27,9 +27,9 @@ struct PassArgs {
     int32_t nx_tiles;         // column pass: nx / COLS
     int32_t ntraj;
     int32_t ncomp;            // column pass: fields per trajectory (3, or 4 for spectra work)
-    const cplx<T>* tw[3];     // stage twiddle tables of the axis for R = 4, 8, 16 points per thread
-    const cplx<T>* ph_pre;    // row pass with a leading half kinetic step: its phase table
-    const cplx<T>* ph;        // phase table exp(-i tau k^2 / 2) / N
+    const twel<T>* tw[3];     // stage twiddle tables of the axis for R = 4, 8, 16 points per thread
+    const twel<T>* ph_pre;    // row pass with a leading half kinetic step: its phase table
+    const twel<T>* ph;        // phase table exp(-i tau k^2 / 2) / N
     LocalCoef<T> coef;        // couplings for the local step (row pass)
 };
 
@@ -37,9 +37,9 @@ template <typename T>
 struct Res1DArgs {
     cplx<T>* const* ptrs;
     int32_t ntraj;
-    const cplx<T>* tw[3];     // stage twiddle tables for R = 4, 8, 16
-    const cplx<T>* ph_full;   // tau = dt
-    const cplx<T>* ph_half;   // tau = dt / 2
+    const twel<T>* tw[3];     // stage twiddle tables for R = 4, 8, 16
+    const twel<T>* ph_full;   // tau = dt
+    const twel<T>* ph_half;   // tau = dt / 2
     T c0, c1, dt;
     double dt_d, t0, q_const, t_end;
     const double* knots;      // device, may be null
@@ -85,7 +85,7 @@ cudaError_t launch_colpass(int n, const PassArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_colfft(int n, const PassArgs<T>& a, cudaStream_t s);
 template <typename T>
-cudaError_t launch_rowfft(int n, cplx<T>* data, int64_t rows, const cplx<T>* const* tw, cudaStream_t s);
+cudaError_t launch_rowfft(int n, cplx<T>* data, int64_t rows, const twel<T>* const* tw, cudaStream_t s);
 template <typename T>
 int colpass_cols(int n);
 template <typename T>

@@ -195,8 +195,9 @@ gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q,
             reinterpret_cast<V* const*>(g.dptrs), t0, W, g.sites, c0, c1, q, w.d_part, w.nblk);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs prep", e);
-        const V* twx[3] = {reinterpret_cast<const V*>(g.tw[0][0]), reinterpret_cast<const V*>(g.tw[0][1]),
-                           reinterpret_cast<const V*>(g.tw[0][2])};
+        const twel<T>* twx[3] = {reinterpret_cast<const twel<T>*>(g.tw[0][0]),
+                                 reinterpret_cast<const twel<T>*>(g.tw[0][1]),
+                                 reinterpret_cast<const twel<T>*>(g.tw[0][2])};
         e = launch_rowfft<T>(g.n[0], W, (int64_t)nc * 4 * g.n[1] * g.n[2], twx, s);
         if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs x fft", e);
         for (int ax = 1; ax < g.ndim; ++ax) {
@@ -205,7 +206,7 @@ gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q,
             a.comp_stride = g.sites;
             a.ntraj = nc;
             a.ncomp = 4;
-            for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const V*>(g.tw[ax][ri]);
+            for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[ax][ri]);
             const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
             if (ax == 1) {
                 a.stride = nx;
@@ -249,6 +250,20 @@ int64_t isqrt_round(int64_t m) {
 }  // namespace
 
 const char* obs_last_error() { return g_obs_err.c_str(); }
+
+int64_t obs_launches(const ObsWork& w, const std::vector<Group>& groups, uint32_t flags) {
+    int64_t n = 0;
+    for (const Group& g : groups) {
+        const int64_t chunk = w.ready ? w.chunk : 0;
+        int64_t max_traj = 0;
+        for (const Group& h : groups) max_traj = std::max<int64_t>(max_traj, h.ntraj);
+        const int64_t c = chunk > 0 ? chunk : max_traj;  // before the first call: estimate
+        const int64_t nchunks = (g.ntraj + c - 1) / c;
+        const int64_t per = 1 + g.ndim + ((flags & GPE_OBS_DIAG) ? 2 : 0) + ((flags & GPE_OBS_SPECTRA) ? 1 : 0);
+        n += nchunks * per;
+    }
+    return n;
+}
 
 gpe_status obs_init(ObsWork& w, const std::vector<Group>& groups, bool f64, int) {
     w.f64 = f64;

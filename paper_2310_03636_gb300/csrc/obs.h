@@ -31,5 +31,7 @@ void obs_free(ObsWork& w);
 gpe_status obs_accumulate(ObsWork& w, const std::vector<Group>& groups, bool f64, double c0, double c1,
                           double q, double* acc, uint32_t flags, int slot, int* d_status, cudaStream_t s);
 const char* obs_last_error();
+// Kernels one obs_accumulate call launches (for the launch counter).
+int64_t obs_launches(const ObsWork& w, const std::vector<Group>& groups, uint32_t flags);
 
 }  // namespace gpe

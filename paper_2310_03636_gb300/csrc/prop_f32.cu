@@ -44,7 +44,7 @@ cudaError_t launch_colfft<float>(int n, const PassArgs<float>& a, cudaStream_t s
 }
 
 template <>
-cudaError_t launch_rowfft<float>(int n, cplx<float>* d, int64_t rows, const cplx<float>* const* tw, cudaStream_t s) {
+cudaError_t launch_rowfft<float>(int n, cplx<float>* d, int64_t rows, const twel<float>* const* tw, cudaStream_t s) {
     switch (n) {
         case 64: return rowfft_n<float, 64>(d, rows, tw, s);
         case 128: return rowfft_n<float, 128>(d, rows, tw, s);

@@ -44,7 +44,7 @@ cudaError_t launch_colfft<double>(int n, const PassArgs<double>& a, cudaStream_t
 }
 
 template <>
-cudaError_t launch_rowfft<double>(int n, cplx<double>* d, int64_t rows, const cplx<double>* const* tw, cudaStream_t s) {
+cudaError_t launch_rowfft<double>(int n, cplx<double>* d, int64_t rows, const twel<double>* const* tw, cudaStream_t s) {
     switch (n) {
         case 64: return rowfft_n<double, 64>(d, rows, tw, s);
         case 128: return rowfft_n<double, 128>(d, rows, tw, s);

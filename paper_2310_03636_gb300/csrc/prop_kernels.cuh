@@ -13,19 +13,23 @@ template <typename T> struct Tune;
 template <> struct Tune<float> {
     static constexpr int kXR = 8;        // points per thread, row pass (3 components live)
     static constexpr int kColR = 16;     // points per thread, column pass
-    static constexpr int kColCols(int n) { return n >= 1024 ? 8 : 16; }
+    static constexpr int kColCols(int n) { return n >= 1024 ? 4 : (n >= 512 ? 8 : 16); }
     static constexpr int kResR(int n) { return n >= 1024 ? 16 : 8; }
     static constexpr int kRowR(int n) { return n >= 256 ? 16 : 8; }
 };
 template <> struct Tune<double> {
     static constexpr int kXR = 4;
     static constexpr int kColR = 8;
-    static constexpr int kColCols(int) { return 8; }
+    static constexpr int kColCols(int n) { return n >= 1024 ? 4 : 8; }
     static constexpr int kResR(int n) { return n >= 1024 ? 8 : 4; }
     static constexpr int kRowR(int n) { return n >= 256 ? 8 : 4; }
 };
 
 template <int R> constexpr int tw_slot() { return R == 4 ? 0 : (R == 8 ? 1 : 2); }
+
+// Offset (in complex elements) of the twiddle block after n data elements, rounded up to
+// 16 bytes so the hi/lo float4 entries are aligned.
+template <typename T> constexpr int tw_off(int n) { return sizeof(T) == 4 ? ((n + 1) & ~1) : n; }
 
 template <int N, int R> constexpr int rows_per_cta() { return (N / R) >= 256 ? 1 : 256 / (N / R); }
 
@@ -41,7 +45,7 @@ k_xpass(const PassArgs<T> a) {
     constexpr int TWN = FftPlan<N, R>::tw_size();
     extern __shared__ __align__(16) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
-    V* tws = sm + RPC * 3 * LD;
+    twel<T>* tws = reinterpret_cast<twel<T>*>(sm + tw_off<T>(RPC * 3 * LD));
     copy_table(tws, a.tw[tw_slot<R>()], TWN);
     const int lrow = threadIdx.x / TP, t = threadIdx.x % TP;
     const int64_t grow = (int64_t)blockIdx.x * RPC + lrow;
@@ -61,9 +65,9 @@ k_xpass(const PassArgs<T> a) {
         fft_pencil<N, R, -1, 3, Sync::Block>(v, buf, tws, t);
 #pragma unroll
         for (int m = 0; m < R; ++m) {
-            const V f = a.ph_pre[t + m * TP];
+            const twel<T> f = a.ph_pre[t + m * TP];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][m] = cmul(v[c][m], f);
+            for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
         }
         fft_pencil<N, R, +1, 3, Sync::Block>(v, buf, tws, t);
     }
@@ -74,9 +78,9 @@ k_xpass(const PassArgs<T> a) {
     fft_pencil<N, R, -1, 3, Sync::Block>(v, buf, tws, t);
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-        const V f = a.ph[t + m * TP];
+        const twel<T> f = a.ph[t + m * TP];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) v[c][m] = cmul(v[c][m], f);
+        for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
     }
     fft_pencil<N, R, +1, 3, Sync::Block>(v, buf, tws, t);
     if (valid) {
@@ -99,7 +103,7 @@ k_colpass(const PassArgs<T> a) {
     constexpr int TWN = FftPlan<N, R>::tw_size();
     extern __shared__ __align__(16) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
-    V* tws = sm + COLS * LD;
+    twel<T>* tws = reinterpret_cast<twel<T>*>(sm + tw_off<T>(COLS * LD));
     copy_table(tws, a.tw[tw_slot<R>()], TWN);
     const int col = threadIdx.x % COLS, t = threadIdx.x / COLS;
     int64_t tile = blockIdx.x;
@@ -118,7 +122,7 @@ k_colpass(const PassArgs<T> a) {
     fft_pencil<N, R, -1, 1, Sync::Block>(v, buf, tws, t);
     if constexpr (!FWD_ONLY) {
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[0][m] = cmul(v[0][m], a.ph[t + m * TP]);
+        for (int m = 0; m < R; ++m) v[0][m] = twmul<-1>(v[0][m], a.ph[t + m * TP]);
         fft_pencil<N, R, +1, 1, Sync::Block>(v, buf, tws, t);
     }
 #pragma unroll
@@ -128,7 +132,7 @@ k_colpass(const PassArgs<T> a) {
 // Forward FFT along x of independent rows (one component per row), in place.
 template <typename T, int N, int R>
 __global__ void __launch_bounds__(rows_per_cta<N, R>() * (N / R))
-k_rowfft(cplx<T>* __restrict__ data, int64_t rows, const cplx<T>* __restrict__ tw) {
+k_rowfft(cplx<T>* __restrict__ data, int64_t rows, const twel<T>* __restrict__ tw) {
     using V = cplx<T>;
     constexpr int TP = N / R;
     constexpr int RPC = rows_per_cta<N, R>();
@@ -136,7 +140,7 @@ k_rowfft(cplx<T>* __restrict__ data, int64_t rows, const cplx<T>* __restrict__ t
     constexpr int TWN = FftPlan<N, R>::tw_size();
     extern __shared__ __align__(16) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
-    V* tws = sm + RPC * LD;
+    twel<T>* tws = reinterpret_cast<twel<T>*>(sm + tw_off<T>(RPC * LD));
     copy_table(tws, tw, TWN);
     const int lrow = threadIdx.x / TP, t = threadIdx.x % TP;
     const int64_t grow = (int64_t)blockIdx.x * RPC + lrow;
@@ -167,7 +171,7 @@ k_resident1d(const Res1DArgs<T> a) {
     constexpr Sync SY = (TP <= 32) ? Sync::Warp : Sync::Block;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
-    V* tws = sm + 3 * LD;
+    twel<T>* tws = reinterpret_cast<twel<T>*>(sm + tw_off<T>(3 * LD));
     copy_table(tws, a.tw[tw_slot<R>()], TWN);
     const int t = threadIdx.x;
     V* base = a.ptrs[blockIdx.x] + t;
@@ -181,9 +185,9 @@ k_resident1d(const Res1DArgs<T> a) {
     fft_pencil<N, R, -1, 3, SY>(v, buf, tws, t);
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-        const V f = a.ph_half[t + m * TP];
+        const twel<T> f = a.ph_half[t + m * TP];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) v[c][m] = cmul(v[c][m], f);
+        for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
     }
     fft_pencil<N, R, +1, 3, SY>(v, buf, tws, t);
     LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt};
@@ -192,12 +196,12 @@ k_resident1d(const Res1DArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < R; ++m) local_step<T>(v[0][m], v[1][m], v[2][m], coef);
         fft_pencil<N, R, -1, 3, SY>(v, buf, tws, t);
-        const V* ph = (s == a.nsteps - 1) ? a.ph_half : a.ph_full;
+        const twel<T>* ph = (s == a.nsteps - 1) ? a.ph_half : a.ph_full;
 #pragma unroll
         for (int m = 0; m < R; ++m) {
-            const V f = ph[t + m * TP];
+            const twel<T> f = ph[t + m * TP];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][m] = cmul(v[c][m], f);
+            for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
         }
         fft_pencil<N, R, +1, 3, SY>(v, buf, tws, t);
     }
@@ -226,7 +230,7 @@ cudaError_t xpass_n(bool pre, const PassArgs<T>& a, cudaStream_t s) {
     constexpr int TP = N / R;
     constexpr int RPC = rows_per_cta<N, R>();
     const int64_t grid = (a.total_rows + RPC - 1) / RPC;
-    const size_t smem = ((size_t)RPC * 3 * smem_ld<T>(N) + FftPlan<N, R>::tw_size()) * sizeof(cplx<T>);
+    const size_t smem = (size_t)tw_off<T>(RPC * 3 * smem_ld<T>(N)) * sizeof(cplx<T>) + FftPlan<N, R>::tw_size() * sizeof(twel<T>);
     if (pre) return launch_with_smem(k_xpass<T, N, R, true, true>, (int)grid, RPC * TP, smem, s, &a);
     return launch_with_smem(k_xpass<T, N, R, false, true>, (int)grid, RPC * TP, smem, s, &a);
 }
@@ -236,17 +240,17 @@ cudaError_t colpass_n(const PassArgs<T>& a, cudaStream_t s) {
     constexpr int R = Tune<T>::kColR;
     constexpr int COLS = Tune<T>::kColCols(N);
     const int64_t grid = (int64_t)a.ntraj * a.ncomp * a.n_outer * a.nx_tiles;
-    const size_t smem = ((size_t)COLS * smem_ld<T>(N) + FftPlan<N, R>::tw_size()) * sizeof(cplx<T>);
+    const size_t smem = (size_t)tw_off<T>(COLS * smem_ld<T>(N)) * sizeof(cplx<T>) + FftPlan<N, R>::tw_size() * sizeof(twel<T>);
     return launch_with_smem(k_colpass<T, N, R, COLS, FWD_ONLY>, (int)grid, COLS * (N / R), smem, s, &a);
 }
 
 template <typename T, int N>
-cudaError_t rowfft_n(cplx<T>* data, int64_t rows, const cplx<T>* const* tw, cudaStream_t s) {
+cudaError_t rowfft_n(cplx<T>* data, int64_t rows, const twel<T>* const* tw, cudaStream_t s) {
     constexpr int R = Tune<T>::kRowR(N);
     constexpr int TP = N / R;
     constexpr int RPC = rows_per_cta<N, R>();
     const int64_t grid = (rows + RPC - 1) / RPC;
-    const size_t smem = ((size_t)RPC * smem_ld<T>(N) + FftPlan<N, R>::tw_size()) * sizeof(cplx<T>);
+    const size_t smem = (size_t)tw_off<T>(RPC * smem_ld<T>(N)) * sizeof(cplx<T>) + FftPlan<N, R>::tw_size() * sizeof(twel<T>);
     auto kern = k_rowfft<T, N, R>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -259,7 +263,7 @@ cudaError_t rowfft_n(cplx<T>* data, int64_t rows, const cplx<T>* const* tw, cuda
 template <typename T, int N>
 cudaError_t resident1d_n(const Res1DArgs<T>& a, cudaStream_t s) {
     constexpr int R = Tune<T>::kResR(N);
-    const size_t smem = ((size_t)3 * smem_ld<T>(N) + FftPlan<N, R>::tw_size()) * sizeof(cplx<T>);
+    const size_t smem = (size_t)tw_off<T>(3 * smem_ld<T>(N)) * sizeof(cplx<T>) + FftPlan<N, R>::tw_size() * sizeof(twel<T>);
     return launch_with_smem(k_resident1d<T, N, R>, a.ntraj, N / R, smem, s, &a);
 }
 
