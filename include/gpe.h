@@ -140,6 +140,11 @@ gpe_status gpe_batch_set_step(gpe_batch* batch, int64_t step);
 gpe_status gpe_profile_enable(gpe_batch* batch, int32_t enable);
 gpe_status gpe_profile_read(gpe_batch* batch, double* ms, int64_t* launches);
 
+/* Verification of the FP32 sine/cosine the local step uses (Cody-Waite reduction plus
+ * Taylor polynomials): for each of n device floats x, writes 4 floats to out (device):
+ * its sin and cos, then CUDA's sincosf of the same x.  Errors: GPE_EINVAL (NULL, n < 0). */
+gpe_status gpe_check_sincos(const float* x, float* out, int64_t n, void* stream);
+
 /* Number of kernels this library has launched since it was loaded (all batches). */
 int64_t gpe_launch_count(void);
 

@@ -58,6 +58,7 @@ def _load():
         "gpe_profile_enable": ([vp, i32], ctypes.c_int),
         "gpe_profile_read": ([vp, pd, ctypes.POINTER(i64)], ctypes.c_int),
         "gpe_launch_count": ([], i64),
+        "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -156,6 +157,15 @@ def gpe_profile_read(h):
 
 def gpe_launch_count():
     return LIB.gpe_launch_count()
+
+
+def gpe_check_sincos(x, stream=None):
+    """x: float32 CUDA tensor -> (n, 4) tensor: own sin, cos, library sin, cos."""
+    assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
+    out = torch.empty((x.numel(), 4), dtype=torch.float32, device=x.device)
+    _check(LIB.gpe_check_sincos(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
+                                _stream(stream)))
+    return out
 
 
 # ----------------------------------------------------------------- convenience

@@ -59,7 +59,38 @@ __device__ __forceinline__ float mulc(float x, double c) {
 }
 __device__ __forceinline__ double mulc(double x, double c) { return x * c; }
 
-__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+static __device__ __noinline__ void sincos_lib(float x, float* s, float* c) { sincosf(x, s, c); }
+
+// sin and cos in FP32 without a slow path: Cody-Waite reduction x = r + q pi/2 with
+// pi/2 split into fl(pi/2) and its remainder, then Taylor polynomials of sin (to r^9)
+// and cos (to r^10) on |r| <= pi/4 (truncation below 3e-9 relative).  |x| > 1e4 goes
+// to the library routine.
+__device__ __forceinline__ void sincos_t(float x, float* s, float* c) {
+    if (fabsf(x) > 1.0e4f) {
+        sincos_lib(x, s, c);
+        return;
+    }
+    const float q = rintf(x * 0.636619772367581343f);
+    float r = fmaf(q, -1.57079637050628662109375f, x);
+    r = fmaf(q, 4.37113900018624283e-8f, r);
+    const float r2 = r * r;
+    float ps = fmaf(r2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);
+    ps = fmaf(ps, r2, 8.33333333333333333e-3f);
+    ps = fmaf(ps, r2, -1.66666666666666667e-1f);
+    const float sn = fmaf(ps * r2, r, r);
+    float pc = fmaf(r2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
+    pc = fmaf(pc, r2, -1.38888888888888889e-3f);
+    pc = fmaf(pc, r2, 4.16666666666666667e-2f);
+    pc = fmaf(pc, r2, -0.5f);
+    const float cs = fmaf(pc, r2, 1.0f);
+    const int iq = (int)q;
+    float so = (iq & 1) ? cs : sn;
+    float co = (iq & 1) ? sn : cs;
+    if (iq & 2) so = -so;
+    if ((iq + 1) & 2) co = -co;
+    *s = so;
+    *c = co;
+}
 __device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }

@@ -217,6 +217,7 @@ PassArgs<T> base_args(const gpe_batch* b, const Group& g) {
     a.comp_stride = g.sites;
     a.ntraj = g.ntraj;
     a.ncomp = 3;
+    a.status = b->d_status;
     a.coef.c0 = (T)b->p.c0;
     a.coef.c1 = (T)b->p.c1;
     a.coef.dt = (T)b->p.dt;

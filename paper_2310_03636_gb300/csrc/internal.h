@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gpe.h"
 #include "local_step.cuh"
 
 namespace gpe {
@@ -31,6 +32,7 @@ struct PassArgs {
     const twel<T>* ph_pre;    // row pass with a leading half kinetic step: its phase table
     const twel<T>* ph;        // phase table exp(-i tau k^2 / 2) / N
     LocalCoef<T> coef;        // couplings for the local step (row pass)
+    int* status;              // device status word (bounded waits that expire)
 };
 
 template <typename T>

@@ -33,6 +33,9 @@ gpe_status obs_fail(gpe_status s, const char* what, cudaError_t e) {
     return s;
 }
 
+// Signed mode number of index i on an axis of n points (n = 1: 0).
+__host__ __device__ __forceinline__ int fold(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
+
 // Fixed-order block sum of NV doubles per thread; result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV * 32 */) {
@@ -118,7 +121,7 @@ k_obs_ekin(const cplx<T>* __restrict__ W, int64_t sites, int nx, int ny, int nz,
         const int ix = (int)(i % nx);
         const int iy = (int)((i / nx) % ny);
         const int iz = (int)(i / ((int64_t)nx * ny));
-        const int jx = ix < nx / 2 ? ix : ix - nx, jy = iy < ny / 2 ? iy : iy - ny, jz = iz < nz / 2 ? iz : iz - nz;
+        const int jx = fold(ix, nx), jy = fold(iy, ny), jz = fold(iz, nz);
         const double kx = gx * jx, ky = gy * jy, kz = gz * jz;
         const V a = w[i];
         const double p = (double)a.x * a.x + (double)a.y * a.y;
@@ -206,6 +209,7 @@ gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q,
             a.comp_stride = g.sites;
             a.ntraj = nc;
             a.ncomp = 4;
+            a.status = d_status;
             for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[ax][ri]);
             const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
             if (ax == 1) {
@@ -280,7 +284,7 @@ gpe_status obs_init(ObsWork& w, const std::vector<Group>& groups, bool f64, int)
     int64_t maxb = 0;
     for (int64_t i = 0; i < g.sites; ++i) {
         const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((int64_t)nx * ny));
-        const int64_t jx = ix < nx / 2 ? ix : ix - nx, jy = iy < ny / 2 ? iy : iy - ny, jz = iz < nz / 2 ? iz : iz - nz;
+        const int64_t jx = fold(ix, nx), jy = fold(iy, ny), jz = fold(iz, nz);
         const int64_t b = isqrt_round(jx * jx + jy * jy + jz * jz);
         bin[i] = (int32_t)b;
         if (b > maxb) maxb = b;

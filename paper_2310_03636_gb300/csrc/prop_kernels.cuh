@@ -4,6 +4,7 @@
 #pragma once
 
 #include "fft.cuh"
+#include "async_copy.cuh"
 #include "internal.h"
 
 namespace gpe {
@@ -12,15 +13,15 @@ namespace gpe {
 template <typename T> struct Tune;
 template <> struct Tune<float> {
     static constexpr int kXR = 8;        // points per thread, row pass (3 components live)
-    static constexpr int kColR = 16;     // points per thread, column pass
-    static constexpr int kColCols(int n) { return n >= 1024 ? 4 : (n >= 512 ? 8 : 16); }
+    static constexpr int kColR(int n) { return n >= 1024 ? 16 : 8; }   // points per thread, column pass
+    static constexpr int kColCols(int n) { return n >= 1024 ? 4 : (n >= 512 ? 4 : (n >= 256 ? 8 : 16)); }
     static constexpr int kResR(int n) { return n >= 1024 ? 16 : 8; }
     static constexpr int kRowR(int n) { return n >= 256 ? 16 : 8; }
 };
 template <> struct Tune<double> {
     static constexpr int kXR = 4;
-    static constexpr int kColR = 8;
-    static constexpr int kColCols(int n) { return n >= 1024 ? 4 : 8; }
+    static constexpr int kColR(int) { return 8; }
+    static constexpr int kColCols(int n) { return n >= 512 ? 4 : 8; }
     static constexpr int kResR(int n) { return n >= 1024 ? 8 : 4; }
     static constexpr int kRowR(int n) { return n >= 256 ? 8 : 4; }
 };
@@ -31,11 +32,42 @@ template <int R> constexpr int tw_slot() { return R == 4 ? 0 : (R == 8 ? 1 : 2);
 // 16 bytes so the hi/lo float4 entries are aligned.
 template <typename T> constexpr int tw_off(int n) { return sizeof(T) == 4 ? ((n + 1) & ~1) : n; }
 
+// Shared-memory length of one column buffer in the column pass: the padded length
+// rounded to a whole 128-byte line plus an offset of (128 B / element) / COLS slots, so a
+// warp (COLS columns x 32 / COLS pencil threads) touches every bank equally.
+template <typename T>
+constexpr int smem_ld_cols(int n, int cols) {
+    return ((n + n / 16 + (int)(64 / sizeof(T)) - 1) / (int)(64 / sizeof(T))) * (int)(64 / sizeof(T)) +
+           ((int)(64 / sizeof(T)) / cols > 0 ? (int)(64 / sizeof(T)) / cols : 1);
+}
+
 template <int N, int R> constexpr int rows_per_cta() { return (N / R) >= 256 ? 1 : 256 / (N / R); }
 
-// Row pass: for each x row of every trajectory (3 components together):
-//   [PRE: FFT_x, x ph_pre, iFFT_x]  [LOCAL: L(dt) per site]  FFT_x, x ph, iFFT_x.
-template <typename T, int N, int R, bool PRE, bool LOCAL>
+constexpr uint32_t kWaitLimit = 1u << 22;   // mbarrier polls before a wait counts as expired
+
+// FFT along x of one row-component held in shared memory (thread t owns positions
+// t + m TP), times a phase table, inverse FFT, back into shared memory.
+template <typename T, int N, int R>
+__device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const twel<T>* tws,
+                                            const twel<T>* __restrict__ ph, int t) {
+    using V = cplx<T>;
+    constexpr int TP = N / R;
+    V v[1][R];
+    V* const xb[1] = {xbuf};
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[0][m] = row[t + m * TP];
+    fft_pencil<N, R, -1, 1, Sync::Block>(v, xb, tws, t);
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[0][m] = twmul<-1>(v[0][m], ph[t + m * TP]);
+    fft_pencil<N, R, +1, 1, Sync::Block>(v, xb, tws, t);
+#pragma unroll
+    for (int m = 0; m < R; ++m) row[t + m * TP] = v[0][m];
+}
+
+// Row pass over RPC x rows of all three components: bulk copies bring the rows into
+// shared memory, then [PRE: Kx(dt/2)] L(dt) per site, Kx(tau) per component, and bulk
+// copies write them back.
+template <typename T, int N, int R, bool PRE>
 __global__ void __launch_bounds__(rows_per_cta<N, R>() * (N / R))
 k_xpass(const PassArgs<T> a) {
     using V = cplx<T>;
@@ -43,52 +75,72 @@ k_xpass(const PassArgs<T> a) {
     constexpr int RPC = rows_per_cta<N, R>();
     constexpr int LD = smem_ld<T>(N);
     constexpr int TWN = FftPlan<N, R>::tw_size();
-    extern __shared__ __align__(16) unsigned char smraw[];
-    V* sm = reinterpret_cast<V*>(smraw);
-    twel<T>* tws = reinterpret_cast<twel<T>*>(sm + tw_off<T>(RPC * 3 * LD));
-    copy_table(tws, a.tw[tw_slot<R>()], TWN);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    V* D = reinterpret_cast<V*>(smraw);                          // [RPC][3][N]
+    V* X = D + RPC * 3 * N;                                      // [RPC][LD] exchange
+    twel<T>* tws = reinterpret_cast<twel<T>*>(X + tw_off<T>(RPC * LD));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tws + TWN);
     const int lrow = threadIdx.x / TP, t = threadIdx.x % TP;
-    const int64_t grow = (int64_t)blockIdx.x * RPC + lrow;
-    const bool valid = grow < a.total_rows;
-    const int64_t g = valid ? grow : 0;
-    const int traj = (int)(g / a.rows_per_traj);
-    const int64_t row = g - (int64_t)traj * a.rows_per_traj;
-    V* base = a.ptrs[traj] + row * N + t;
-    V* const buf[3] = {sm + (lrow * 3 + 0) * LD, sm + (lrow * 3 + 1) * LD, sm + (lrow * 3 + 2) * LD};
-    V v[3][R];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int m = 0; m < R; ++m) v[c][m] = valid ? base[c * a.comp_stride + m * TP] : mk((T)0, (T)0);
+    const int64_t row0 = (int64_t)blockIdx.x * RPC;
+    const int nrows = (int)min((int64_t)RPC, a.total_rows - row0);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
-    if constexpr (PRE) {
-        fft_pencil<N, R, -1, 3, Sync::Block>(v, buf, tws, t);
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, (uint32_t)(nrows * 3 * N * sizeof(V)));
+        for (int r = 0; r < nrows; ++r) {
+            const int64_t g = row0 + r;
+            const int traj = (int)(g / a.rows_per_traj);
+            const V* src = a.ptrs[traj] + (g - (int64_t)traj * a.rows_per_traj) * N;
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const twel<T> f = a.ph_pre[t + m * TP];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
+            for (int c = 0; c < 3; ++c)
+                bulk_g2s(D + (r * 3 + c) * N, src + c * a.comp_stride, N * sizeof(V), bar);
         }
-        fft_pencil<N, R, +1, 3, Sync::Block>(v, buf, tws, t);
     }
-    if constexpr (LOCAL) {
-#pragma unroll
-        for (int m = 0; m < R; ++m) local_step<T>(v[0][m], v[1][m], v[2][m], a.coef);
+    copy_table(tws, a.tw[tw_slot<R>()], TWN);
+    const bool ok = __syncthreads_and(mbar_wait(bar, 0, kWaitLimit));
+    if (!ok) {
+        if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)GPE_ETIMEOUT);
+        mbar_wait(bar, 0, kWaitLimit);
+        return;
     }
-    fft_pencil<N, R, -1, 3, Sync::Block>(v, buf, tws, t);
-#pragma unroll
-    for (int m = 0; m < R; ++m) {
-        const twel<T> f = a.ph[t + m * TP];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
+    V* Dr = D + lrow * 3 * N;
+    V* Xr = X + lrow * LD;
+    if constexpr (PRE) {
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) kinetic_row<T, N, R>(Dr + c * N, Xr, tws, a.ph_pre, t);
     }
-    fft_pencil<N, R, +1, 3, Sync::Block>(v, buf, tws, t);
-    if (valid) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int m = 0; m < R; ++m) base[c * a.comp_stride + m * TP] = v[c][m];
+    if (lrow < nrows) {
+#pragma unroll 2
+        for (int m = 0; m < R; ++m) {
+            const int i = t + m * TP;
+            V p1 = Dr[i], p0 = Dr[N + i], pm = Dr[2 * N + i];
+            local_step<T>(p1, p0, pm, a.coef);
+            Dr[i] = p1;
+            Dr[N + i] = p0;
+            Dr[2 * N + i] = pm;
+        }
     }
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) kinetic_row<T, N, R>(Dr + c * N, Xr, tws, a.ph, t);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < nrows; ++r) {
+            const int64_t g = row0 + r;
+            const int traj = (int)(g / a.rows_per_traj);
+            V* dst = a.ptrs[traj] + (g - (int64_t)traj * a.rows_per_traj) * N;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) bulk_s2g(dst + c * a.comp_stride, D + (r * 3 + c) * N, N * sizeof(V));
+        }
+        bulk_commit();
+        bulk_wait_read_all();
+    }
+}
+
+template <typename T, int N, int R>
+constexpr size_t xpass_smem() {
+    return ((size_t)rows_per_cta<N, R>() * 3 * N + tw_off<T>(rows_per_cta<N, R>() * smem_ld<T>(N))) * sizeof(cplx<T>) +
+           FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
 }
 
 // Column pass: pencils of length N along a strided axis, COLS adjacent x columns per
@@ -99,9 +151,9 @@ __global__ void __launch_bounds__(COLS * (N / R))
 k_colpass(const PassArgs<T> a) {
     using V = cplx<T>;
     constexpr int TP = N / R;
-    constexpr int LD = smem_ld<T>(N);
+    constexpr int LD = smem_ld_cols<T>(N, COLS);
     constexpr int TWN = FftPlan<N, R>::tw_size();
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
     twel<T>* tws = reinterpret_cast<twel<T>*>(sm + tw_off<T>(COLS * LD));
     copy_table(tws, a.tw[tw_slot<R>()], TWN);
@@ -138,7 +190,7 @@ k_rowfft(cplx<T>* __restrict__ data, int64_t rows, const twel<T>* __restrict__ t
     constexpr int RPC = rows_per_cta<N, R>();
     constexpr int LD = smem_ld<T>(N);
     constexpr int TWN = FftPlan<N, R>::tw_size();
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
     twel<T>* tws = reinterpret_cast<twel<T>*>(sm + tw_off<T>(RPC * LD));
     copy_table(tws, tw, TWN);
@@ -169,7 +221,7 @@ k_resident1d(const Res1DArgs<T> a) {
     constexpr int LD = smem_ld<T>(N);
     constexpr int TWN = FftPlan<N, R>::tw_size();
     constexpr Sync SY = (TP <= 32) ? Sync::Warp : Sync::Block;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
     twel<T>* tws = reinterpret_cast<twel<T>*>(sm + tw_off<T>(3 * LD));
     copy_table(tws, a.tw[tw_slot<R>()], TWN);
@@ -230,17 +282,18 @@ cudaError_t xpass_n(bool pre, const PassArgs<T>& a, cudaStream_t s) {
     constexpr int TP = N / R;
     constexpr int RPC = rows_per_cta<N, R>();
     const int64_t grid = (a.total_rows + RPC - 1) / RPC;
-    const size_t smem = (size_t)tw_off<T>(RPC * 3 * smem_ld<T>(N)) * sizeof(cplx<T>) + FftPlan<N, R>::tw_size() * sizeof(twel<T>);
-    if (pre) return launch_with_smem(k_xpass<T, N, R, true, true>, (int)grid, RPC * TP, smem, s, &a);
-    return launch_with_smem(k_xpass<T, N, R, false, true>, (int)grid, RPC * TP, smem, s, &a);
+    const size_t smem = xpass_smem<T, N, R>();
+    if (pre) return launch_with_smem(k_xpass<T, N, R, true>, (int)grid, RPC * TP, smem, s, &a);
+    return launch_with_smem(k_xpass<T, N, R, false>, (int)grid, RPC * TP, smem, s, &a);
 }
 
 template <typename T, int N, bool FWD_ONLY>
 cudaError_t colpass_n(const PassArgs<T>& a, cudaStream_t s) {
-    constexpr int R = Tune<T>::kColR;
+    constexpr int R = Tune<T>::kColR(N);
     constexpr int COLS = Tune<T>::kColCols(N);
     const int64_t grid = (int64_t)a.ntraj * a.ncomp * a.n_outer * a.nx_tiles;
-    const size_t smem = (size_t)tw_off<T>(COLS * smem_ld<T>(N)) * sizeof(cplx<T>) + FftPlan<N, R>::tw_size() * sizeof(twel<T>);
+    const size_t smem = (size_t)tw_off<T>(COLS * smem_ld_cols<T>(N, COLS)) * sizeof(cplx<T>) +
+                        FftPlan<N, R>::tw_size() * sizeof(twel<T>);
     return launch_with_smem(k_colpass<T, N, R, COLS, FWD_ONLY>, (int)grid, COLS * (N / R), smem, s, &a);
 }
 

@@ -301,3 +301,23 @@ def test_full_size_2d_512_sampled(B):
         ref = run_oracle(oracle_initial(wl.shape, 1, seed, ids=[t]), wl.dt, 60, 2)
         assert rel_l2_per_comp(gpu, ref) <= 1e-4
     b.close()
+
+
+def test_own_sincos_against_cuda(B):
+    """The local step's FP32 sin/cos (Cody-Waite + Taylor) stays within 2 ulp-scale of
+    CUDA's sincosf and of the FP64 value, over small, typical and large arguments."""
+    g = torch.Generator().manual_seed(3)
+    xs = torch.cat([torch.linspace(-4, 4, 200001), (torch.rand(200000, generator=g) - 0.5) * 2e4,
+                    torch.tensor([0.0, -0.0, 1e-30, 1e4, -1e4, 3e4, 1e6, float(np.pi) / 4, 1e-6])]).float()
+    out = B.gpe_check_sincos(xs.cuda()).cpu().double()
+    x64 = xs.double()
+    s_ref, c_ref = torch.sin(x64), torch.cos(x64)
+    assert (out[:, 0] - s_ref).abs().max() < 3e-7 * max(1.0, 1.0)
+    assert (out[:, 1] - c_ref).abs().max() < 3e-7
+    # relative accuracy of sin for small arguments (the common case in the local step)
+    small = xs.abs() < 0.5
+    rel = ((out[small, 0] - s_ref[small]).abs() / s_ref[small].abs().clamp_min(1e-30))
+    assert rel.max() < 2.5e-7
+    # never worse than the library by more than 1.5e-7 absolute
+    assert (out[:, 0] - s_ref).abs().max() <= (out[:, 2] - s_ref).abs().max() + 1.5e-7
+    assert (out[:, 1] - c_ref).abs().max() <= (out[:, 3] - c_ref).abs().max() + 1.5e-7
