@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ncu-case", action="store_true",
+                   help="small profiling target: the 512^2 x 64 batch (403 MB > L2), 4 steps + observables")
     return p.parse_args()
 
 
@@ -340,9 +342,27 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def ncu_case():
+    """Short run of the benchmark workload for ncu captures: noise, 4 steps, one observables call."""
+    from paper_2310_03636_gb300 import binding as B
+    b = B.GPEBatch(WL.shape, WL.ntraj, "c64", WL.c0, WL.c1, WL.q, WL.dt, dx=WL.dx)
+    b.init_noise(W.SEED_BASE, WL.mean_spinor(), WL.noise_per_mode)
+    b.step(4)
+    acc = b.new_accumulator(1)
+    b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 0)
+    torch.cuda.synchronize()
+    st = b.sync_status()
+    b.close()
+    print(json.dumps({"ncu_case": WL.name, "status": st}))
+    if st != B.GPE_OK:
+        sys.exit(1)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.ncu_case:
+        ncu_case()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
