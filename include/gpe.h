@@ -140,6 +140,25 @@ gpe_status gpe_batch_set_step(gpe_batch* batch, int64_t step);
 gpe_status gpe_profile_enable(gpe_batch* batch, int32_t enable);
 gpe_status gpe_profile_read(gpe_batch* batch, double* ms, int64_t* launches);
 
+/* Real-space diagnostics that allocate no device memory (the paper has no counterpart;
+ * this is a service entry point).  For callers that cannot let the library allocate:
+ * code that must not synchronise the device (cudaMalloc and cudaFree can), a process
+ * whose device memory is all handed out by another allocator, or a health check run
+ * while the device is out of memory.  psi: ntraj caller-owned fields laid out back to
+ * back, each [3][n2][n1][n0] complex (dtype), 16-byte aligned.  out: caller-owned device
+ * array of ntraj * 8 doubles, overwritten (not accumulated) with
+ * (N_1, N_0, N_-1, 0, E_q, E_c0, E_c1, 0) per trajectory -- the diagnostics record of
+ * observables_accumulate without the kinetic energy.  Partial sums live in a fixed
+ * 192 KiB array compiled into the library (held on every device that loads it until the
+ * process exits); capacity: ntraj * ceil(sites / 4096) <= 4096 site blocks, larger
+ * requests return GPE_EINVAL with a message.  The first call on a device looks up the
+ * array's device address, so make it before any stream capture.  Calls share the array:
+ * calls that overlap on the same GPU race; serialise them.  Errors: GPE_EINVAL (NULL or
+ * misaligned pointers, bad sizes, capacity), GPE_ECUDA. */
+gpe_status gpe_diagnostics_noalloc(const void* psi, int32_t ntraj, int32_t ndim, const int32_t n[3],
+                                   double dx, gpe_dtype dtype, double c0, double c1, double q,
+                                   double* out, void* stream);
+
 /* Verification of the FP32 sine/cosine the local step uses (Cody-Waite reduction plus
  * Taylor polynomials): for each of n device floats x, writes 4 floats to out (device):
  * its sin and cos, then CUDA's sincosf of the same x.  Errors: GPE_EINVAL (NULL, n < 0). */

@@ -59,6 +59,8 @@ def _load():
         "gpe_profile_read": ([vp, pd, ctypes.POINTER(i64)], ctypes.c_int),
         "gpe_launch_count": ([], i64),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
+        "gpe_diagnostics_noalloc": ([vp, i32, i32, ctypes.POINTER(i32), dbl, ctypes.c_int, dbl, dbl, dbl, vp, vp],
+                                    ctypes.c_int),
         "gpe_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -157,6 +159,18 @@ def gpe_profile_read(h):
 
 def gpe_launch_count():
     return LIB.gpe_launch_count()
+
+
+def gpe_diagnostics_noalloc(psi, ndim, c0, c1, q, dx, out, stream=None):
+    """psi: (ntraj, 3, *shape) complex CUDA tensor; out: (ntraj * 8,) float64 CUDA tensor."""
+    assert psi.is_cuda and psi.is_contiguous() and out.dtype == torch.float64 and out.is_cuda
+    shape = tuple(psi.shape[2:])
+    assert len(shape) == ndim
+    n = (ctypes.c_int32 * 3)(*(list(reversed(shape)) + [1] * (3 - ndim)))
+    dt = GPE_C64 if psi.dtype == torch.complex64 else GPE_C128
+    _check(LIB.gpe_diagnostics_noalloc(ctypes.c_void_p(psi.data_ptr()), psi.shape[0], ndim, n, float(dx), dt,
+                                       float(c0), float(c1), float(q), ctypes.c_void_p(out.data_ptr()),
+                                       _stream(stream)))
 
 
 def gpe_check_sincos(x, stream=None):

@@ -60,6 +60,8 @@ struct Profiler {
 
 }  // namespace
 
+void gpe::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct gpe_batch {
     gpe_dtype dtype;
     gpe_params p;

@@ -75,6 +75,9 @@ struct Group {
     void* ph_half[3] = {};         // per axis: exp(-i dt k^2/4)/n
 };
 
+// Sets the message gpe_last_error() returns on this thread.
+void set_last_error(const char* msg);
+
 template <typename T> int xpass_max_n();
 template <typename T> int colpass_max_n();
 template <typename T> int resident1d_max_n();
