@@ -77,12 +77,109 @@ __device__ __forceinline__ void offdiag_mix(V& p1, V& p0, V& pm, T c1, T dt) {
     pm = mk(pm.x + e1 * um.y - e2 * wm.x, pm.y - e1 * um.x - e2 * wm.y);
 }
 
+// sin and cos of x: Taylor polynomials for |x| <= 1/2 (truncation below 2e-11),
+// otherwise the range-reduced routine.
+__device__ __forceinline__ void sincos_small(float x, float* s, float* c) {
+    if (fabsf(x) > 0.5f) {
+        sincos_t(x, s, c);
+        return;
+    }
+    const float x2 = x * x;
+    float ps = fmaf(x2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);
+    ps = fmaf(ps, x2, 8.33333333333333333e-3f);
+    ps = fmaf(ps, x2, -1.66666666666666667e-1f);
+    *s = fmaf(ps * x2, x, x);
+    float pc = fmaf(x2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
+    pc = fmaf(pc, x2, -1.38888888888888889e-3f);
+    pc = fmaf(pc, x2, 4.16666666666666667e-2f);
+    pc = fmaf(pc, x2, -0.5f);
+    *c = fmaf(pc, x2, 1.0f);
+}
+
+__device__ __forceinline__ float2 rot_minus(float2 p, float ang) {
+    float s, c;
+    sincos_small(ang, &s, &c);
+    return make_float2(p.x * c + p.y * s, p.y * c - p.x * s);
+}
+
+// FP32 local step, same operator as D(dt/2) O(dt) D(dt/2) but arranged for fewer
+// transcendental evaluations:
+//  * a common phase of all three components commutes with O (a and b are invariant),
+//    so each D applies the m = +-1 phases relative to m = 0 and the two m = 0 phases
+//    are applied once at the end;
+//  * the O coefficients sin(th)/th and (1 - cos th)/th^2 are even in th, so they are
+//    power series in u = th^2 = lambda^2 (c1 dt)^2 (no square root or division):
+//    sum (-u)^k / (2k+1)! and sum (-u)^k / (2k+2)! to k = 4 for u <= 1/4 (truncation
+//    below 3e-11), the trigonometric form otherwise.
+__device__ __forceinline__ void local_step_fast(float2& p1, float2& p0, float2& pm, const LocalCoef<float>& k) {
+    const float h = 0.5f * k.dt;
+    const float c0 = k.c0, c1 = k.c1, q = k.q;
+    // D(dt/2), relative to m = 0
+    float n1 = cabs2(p1), n0 = cabs2(p0), nm = cabs2(pm);
+    const float g0 = ((c0 + c1) * (n1 + n0 + nm) - c1 * n0) * h;
+    p1 = rot_minus(p1, (q - 2.0f * c1 * nm + c1 * n0) * h);
+    pm = rot_minus(pm, (q - 2.0f * c1 * n1 + c1 * n0) * h);
+    // O(dt)
+    const float eps = c1 * k.dt;
+    const float2 a = cmulc(pm, p0);
+    const float2 b = cmulc(p0, p1);
+    const float2 s1 = cmul(a, p0);
+    const float2 s0 = cadd(cmulc(a, p1), cmul(b, pm));
+    const float2 sm = cmulc(b, p0);
+    const float2 t1 = make_float2(fmaf(eps, s1.y, p1.x), fmaf(-eps, s1.x, p1.y));
+    const float2 t0 = make_float2(fmaf(eps, s0.y, p0.x), fmaf(-eps, s0.x, p0.y));
+    const float2 tm = make_float2(fmaf(eps, sm.y, pm.x), fmaf(-eps, sm.x, pm.y));
+    const float2 A = cscale(cadd(a, cmulc(tm, t0)), 0.5f);
+    const float2 B = cscale(cadd(b, cmulc(t0, t1)), 0.5f);
+    const float u = (cabs2(A) + cabs2(B)) * (eps * eps);
+    float f1, f2;
+    if (u <= 0.25f) {
+        f1 = fmaf(u, 2.75573192239858907e-6f, -1.98412698412698413e-4f);
+        f1 = fmaf(f1, u, 8.33333333333333333e-3f);
+        f1 = fmaf(f1, u, -1.66666666666666667e-1f);
+        f1 = fmaf(f1, u, 1.0f);
+        f2 = fmaf(u, 2.75573192239858907e-7f, -2.48015873015873016e-5f);
+        f2 = fmaf(f2, u, 1.38888888888888889e-3f);
+        f2 = fmaf(f2, u, -4.16666666666666667e-2f);
+        f2 = fmaf(f2, u, 0.5f);
+    } else {
+        const float x = 0.5f * sqrtf(u);
+        float sx, cx;
+        sincos_t(x, &sx, &cx);
+        const float r = sx / x;
+        f1 = r * cx;
+        f2 = 0.5f * r * r;
+    }
+    const float e1 = eps * f1, e2 = eps * eps * f2;
+    const float2 u1 = cmul(A, p0);
+    const float2 u0 = cadd(cmulc(A, p1), cmul(B, pm));
+    const float2 um = cmulc(B, p0);
+    const float2 w1 = cmul(A, u0);
+    const float2 w0 = cadd(cmulc(A, u1), cmul(B, um));
+    const float2 wm = cmulc(B, u0);
+    p1 = make_float2(p1.x + e1 * u1.y - e2 * w1.x, p1.y - e1 * u1.x - e2 * w1.y);
+    p0 = make_float2(p0.x + e1 * u0.y - e2 * w0.x, p0.y - e1 * u0.x - e2 * w0.y);
+    pm = make_float2(pm.x + e1 * um.y - e2 * wm.x, pm.y - e1 * um.x - e2 * wm.y);
+    // D(dt/2) with the deferred m = 0 phases of both halves
+    n1 = cabs2(p1);
+    n0 = cabs2(p0);
+    nm = cabs2(pm);
+    const float gg = g0 + ((c0 + c1) * (n1 + n0 + nm) - c1 * n0) * h;
+    p1 = rot_minus(p1, gg + (q - 2.0f * c1 * nm + c1 * n0) * h);
+    pm = rot_minus(pm, gg + (q - 2.0f * c1 * n1 + c1 * n0) * h);
+    p0 = rot_minus(p0, gg);
+}
+
 template <typename T, typename V>
 __device__ __forceinline__ void local_step(V& p1, V& p0, V& pm, const LocalCoef<T>& k) {
-    const T h = (T)0.5 * k.dt;
-    diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h);
-    offdiag_mix<T>(p1, p0, pm, k.c1, k.dt);
-    diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h);
+    if constexpr (sizeof(T) == 4) {
+        local_step_fast(p1, p0, pm, k);
+    } else {
+        const T h = (T)0.5 * k.dt;
+        diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h);
+        offdiag_mix<T>(p1, p0, pm, k.c1, k.dt);
+        diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h);
+    }
 }
 
 }  // namespace gpe
