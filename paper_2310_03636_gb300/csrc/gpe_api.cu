@@ -11,6 +11,8 @@
 #include <tuple>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "gpe.h"
 #include "internal.h"
 #include "obs.h"
@@ -61,6 +63,57 @@ struct Profiler {
 }  // namespace
 
 void gpe::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+}  // namespace
+
+// Tensor maps over a contiguous group: y pencils through a 2D view {2 nx, ntraj 3 nz ny}
+// of the whole batch, z pencils through a 3D view {2 nx, ny, nz 3 ntraj}; boxes are
+// COLS complex columns wide and min(n, 256) points long.
+bool gpe::encode_group_maps(Group& g, int eb, int cols_y, int cols_z) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || g.ndim < 2) return false;
+    const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const cuuint32_t es[3] = {1, 1, 1};
+    {
+        const cuuint64_t dims[2] = {2 * nx, (cuuint64_t)g.ntraj * 3 * nz * ny};
+        const cuuint64_t strides[1] = {2 * nx * (cuuint64_t)eb};
+        const cuuint32_t box[2] = {(cuuint32_t)(2 * cols_y), (cuuint32_t)(ny < 256 ? ny : 256)};
+        if (enc(&g.map_y, dt, 2, g.hptrs[0], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    if (g.ndim == 3) {
+        const cuuint64_t dims[3] = {2 * nx, ny, nz * 3 * (cuuint64_t)g.ntraj};
+        const cuuint64_t strides[2] = {2 * nx * (cuuint64_t)eb, 2 * nx * ny * (cuuint64_t)eb};
+        const cuuint32_t box[3] = {(cuuint32_t)(2 * cols_z), 1, (cuuint32_t)(nz < 256 ? nz : 256)};
+        if (enc(&g.map_z, dt, 3, g.hptrs[0], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
 
 struct gpe_batch {
     gpe_dtype dtype;
@@ -231,6 +284,17 @@ PassArgs<T> base_args(const gpe_batch* b, const Group& g) {
 template <typename T>
 cudaError_t col_pass(gpe_batch* b, const Group& g, int ax, bool half, cudaStream_t s) {
     ProfScope ps(b, 1, s, 1);
+    if (g.contiguous) {
+        const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+        const int nxt = nx / colpass_cols<T>(g.n[ax]);
+        const int n_tiles = ax == 1 ? nxt * g.ntraj * 3 * nz : nxt * ny * g.ntraj * 3;
+        const twel<T>* tws[3] = {reinterpret_cast<const twel<T>*>(g.tw[ax][0]),
+                                 reinterpret_cast<const twel<T>*>(g.tw[ax][1]),
+                                 reinterpret_cast<const twel<T>*>(g.tw[ax][2])};
+        return launch_colpass_tma<T>(g.n[ax], ax, false, ax == 1 ? g.map_y : g.map_z, n_tiles, nxt, ny, tws,
+                                     reinterpret_cast<const twel<T>*>(half ? g.ph_half[ax] : g.ph_full[ax]),
+                                     b->d_status, s);
+    }
     PassArgs<T> a = base_args<T>(b, g);
     for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[ax][ri]);
     a.ph = reinterpret_cast<const twel<T>*>(half ? g.ph_half[ax] : g.ph_full[ax]);
@@ -383,6 +447,17 @@ gpe_status gpe_batch_create(const gpe_traj* trajs, int32_t ntraj, gpe_dtype dtyp
             return cleanup(fail(GPE_ECUDA, "copy group tables"));
         s = (dtype == GPE_C64) ? build_group_tables<float>(b, g) : build_group_tables<double>(b, g);
         if (s != GPE_OK) return cleanup(s);
+        const size_t vb = (dtype == GPE_C64) ? 8 : 16;
+        bool contiguous = g.ndim >= 2;
+        for (int i = 1; i < g.ntraj && contiguous; ++i)
+            contiguous = (char*)g.hptrs[i] == (char*)g.hptrs[0] + (size_t)i * 3 * g.sites * vb;
+        if (contiguous) {
+            const int cy = (dtype == GPE_C64) ? colpass_cols<float>(g.n[1]) : colpass_cols<double>(g.n[1]);
+            const int cz = g.ndim == 3 ? ((dtype == GPE_C64) ? colpass_cols<float>(g.n[2]) : colpass_cols<double>(g.n[2]))
+                                       : cy;
+            contiguous = encode_group_maps(g, (int)(vb / 2), cy, cz);
+        }
+        g.contiguous = contiguous;
     }
     if ((s = obs_init(b->obs, b->groups, b->dtype == GPE_C128, b->device)) != GPE_OK) {
         g_err = obs_last_error();

@@ -1,6 +1,7 @@
 // Internal (non-ABI) declarations shared by the kernel translation units and the C-ABI layer.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -73,6 +74,9 @@ struct Group {
     void* tw[3][3] = {};           // per axis: stage twiddle tables for R = 4, 8, 16
     void* ph_full[3] = {};         // per axis: exp(-i dt k^2/2)/n
     void* ph_half[3] = {};         // per axis: exp(-i dt k^2/4)/n
+    bool contiguous = false;       // fields back to back from hptrs[0]: tensor-map passes usable
+    CUtensorMap map_y{};           // 2D map {2 nx, ntraj 3 nz ny} of the batch (ndim >= 2)
+    CUtensorMap map_z{};           // 3D map {2 nx, ny, nz 3 ntraj} (ndim == 3)
 };
 
 // Sets the message gpe_last_error() returns on this thread.
@@ -93,6 +97,12 @@ template <typename T>
 cudaError_t launch_rowfft(int n, cplx<T>* data, int64_t rows, const twel<T>* const* tw, cudaStream_t s);
 template <typename T>
 int colpass_cols(int n);
+// Persistent TMA column pass over a contiguous group: axis 1 (y) or 2 (z).
+template <typename T>
+cudaError_t launch_colpass_tma(int n, int axis, bool fwd_only, const CUtensorMap& map, int n_tiles, int nx_tiles,
+                               int ny, const twel<T>* tw4_8_16[3], const twel<T>* ph, int* status, cudaStream_t s);
+// Encodes the tensor maps of a contiguous group (elements of ``elem_bytes`` per real).
+bool encode_group_maps(Group& g, int elem_bytes, int cols_y, int cols_z);
 template <typename T>
 cudaError_t launch_resident1d(int n, const Res1DArgs<T>& a, cudaStream_t s);
 template <typename T>

@@ -59,3 +59,39 @@ cudaError_t launch_rowfft<float>(int n, cplx<float>* d, int64_t rows, const twel
 }
 
 }  // namespace gpe
+
+namespace gpe {
+
+template <>
+cudaError_t launch_colpass_tma<float>(int n, int axis, bool fwd_only, const CUtensorMap& map, int n_tiles, int nx_tiles,
+                                  int ny, const twel<float>* tws[3], const twel<float>* ph, int* status, cudaStream_t s) {
+    ColTmaArgs<float> a{};
+    a.n_tiles = n_tiles;
+    a.nx_tiles = nx_tiles;
+    a.ny = ny;
+    a.ph = ph;
+    a.status = status;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = n_tiles < 2 * sms ? n_tiles : 2 * sms;
+#define GPE_COLTMA(NN)                                                                                     \
+    case NN: {                                                                                             \
+        a.tw = tws[tw_slot<Tune<float>::kColR(NN)>()];                                                        \
+        if (axis == 2) return fwd_only ? colpass_tma_n<float, NN, true, true>(map, a, grid, s)                \
+                                       : colpass_tma_n<float, NN, false, true>(map, a, grid, s);              \
+        return fwd_only ? colpass_tma_n<float, NN, true, false>(map, a, grid, s)                              \
+                        : colpass_tma_n<float, NN, false, false>(map, a, grid, s);                            \
+    }
+    switch (n) {
+        GPE_COLTMA(64)
+        GPE_COLTMA(128)
+        GPE_COLTMA(256)
+        GPE_COLTMA(512)
+        GPE_COLTMA(1024)
+        default: return cudaErrorInvalidValue;
+    }
+#undef GPE_COLTMA
+}
+
+}  // namespace gpe

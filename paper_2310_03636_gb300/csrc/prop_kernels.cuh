@@ -4,6 +4,8 @@
 #pragma once
 
 #include "fft.cuh"
+#include <cuda.h>
+
 #include "async_copy.cuh"
 #include "internal.h"
 
@@ -181,6 +183,132 @@ k_colpass(const PassArgs<T> a) {
     for (int m = 0; m < R; ++m) base[(int64_t)m * TP * a.stride] = v[0][m];
 }
 
+// Column pass over a contiguous batch, persistent and pipelined: each block walks its
+// tiles (COLS adjacent x columns x N pencil points of one component), the TMA engine
+// loads tile i+1 while tile i is transformed, and stores each finished tile back through
+// the same tensor map.  ZPASS: pencils along z of a 3D map {2 nx, ny, nz 3 ntraj};
+// otherwise pencils along y of a 2D map {2 nx, rows}.  FWD_ONLY: forward FFT only.
+template <typename T>
+struct ColTmaArgs {
+    int32_t n_tiles;     // tiles in the whole launch
+    int32_t nx_tiles;    // nx / COLS
+    int32_t ny;          // ZPASS: points along y (tile -> y, component-trajectory)
+    const twel<T>* tw;   // stage twiddles of FftPlan<N, R>
+    const twel<T>* ph;   // phase table (unused when FWD_ONLY)
+    int* status;
+};
+
+template <typename T, int N, int COLS>
+constexpr size_t colpass_tma_smem(int R) {
+    return (size_t)2 * N * COLS * sizeof(cplx<T>) + (size_t)tw_off<T>(COLS * smem_ld_cols<T>(N, COLS)) * sizeof(cplx<T>);
+}
+
+template <typename T, int N, int R, int COLS, bool FWD_ONLY, bool ZPASS>
+__global__ void __launch_bounds__(COLS * (N / R))
+k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
+    using V = cplx<T>;
+    constexpr int TP = N / R;
+    constexpr int LD = smem_ld_cols<T>(N, COLS);
+    constexpr int TWN = FftPlan<N, R>::tw_size();
+    constexpr int BOX = N < 256 ? N : 256;
+    constexpr int NBOX = N / BOX;
+    constexpr uint32_t TILE_BYTES = (uint32_t)(N * COLS * sizeof(V));
+    extern __shared__ __align__(128) unsigned char smraw[];
+    V* buf = reinterpret_cast<V*>(smraw);                                   // [2][N][COLS]
+    V* X = buf + 2 * N * COLS;                                              // [COLS][LD]
+    twel<T>* tws = reinterpret_cast<twel<T>*>(X + tw_off<T>(COLS * LD));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tws + TWN);
+    const int col = threadIdx.x % COLS, t = threadIdx.x / COLS;
+    const void* map = &tmap;
+
+    auto coords = [&](int tile, int& c0, int& c1, int& c2) {
+        const int xt = tile % a.nx_tiles;
+        const int rest = tile / a.nx_tiles;
+        c0 = xt * 2 * COLS;
+        if constexpr (ZPASS) {
+            c1 = rest % a.ny;
+            c2 = (rest / a.ny) * N;
+        } else {
+            c1 = rest * N;
+            c2 = 0;
+        }
+    };
+    auto issue_load = [&](int tile, int st) {
+        int c0, c1, c2;
+        coords(tile, c0, c1, c2);
+        V* dst = buf + st * N * COLS;
+        mbar_expect_tx(&bar[st], TILE_BYTES);
+#pragma unroll
+        for (int b = 0; b < NBOX; ++b) {
+            if constexpr (ZPASS) tma_load_3d(dst + b * BOX * COLS, map, c0, c1, c2 + b * BOX, &bar[st]);
+            else tma_load_2d(dst + b * BOX * COLS, map, c0, c1 + b * BOX, &bar[st]);
+        }
+    };
+    auto issue_store = [&](int tile, int st) {
+        int c0, c1, c2;
+        coords(tile, c0, c1, c2);
+        const V* src = buf + st * N * COLS;
+#pragma unroll
+        for (int b = 0; b < NBOX; ++b) {
+            if constexpr (ZPASS) tma_store_3d(map, c0, c1, c2 + b * BOX, src + b * BOX * COLS);
+            else tma_store_2d(map, c0, c1 + b * BOX, src + b * BOX * COLS);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    const int first = blockIdx.x, stride = gridDim.x;
+    if (threadIdx.x == 0) {
+        if (first < a.n_tiles) issue_load(first, 0);
+        if (first + stride < a.n_tiles) issue_load(first + stride, 1);
+    }
+    copy_table(tws, a.tw, TWN);
+    __syncthreads();
+    V* const xb[1] = {X + col * LD};
+    int it = 0;
+    bool ok = true;
+    for (int tile = first; tile < a.n_tiles; tile += stride, ++it) {
+        const int st = it & 1;
+        V* bs = buf + st * N * COLS;
+        ok = __syncthreads_and(mbar_wait(&bar[st], (uint32_t)((it >> 1) & 1), kWaitLimit));
+        if (!ok) break;
+        V v[1][R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[0][m] = bs[(t + m * TP) * COLS + col];
+        fft_pencil<N, R, -1, 1, Sync::Block>(v, xb, tws, t);
+        if constexpr (!FWD_ONLY) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[0][m] = twmul<-1>(v[0][m], a.ph[t + m * TP]);
+            fft_pencil<N, R, +1, 1, Sync::Block>(v, xb, tws, t);
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) bs[(t + m * TP) * COLS + col] = v[0][m];
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            issue_store(tile, st);
+            bulk_commit();
+            const int nxt = tile + 2 * stride;
+            if (nxt < a.n_tiles) {
+                bulk_wait_read_all();
+                issue_load(nxt, st);
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (!ok) {
+            atomicCAS(a.status, 0, (int)GPE_ETIMEOUT);
+            // let copies still in flight land before the block's shared memory goes away
+            mbar_wait(&bar[it & 1], (uint32_t)((it >> 1) & 1), kWaitLimit);
+            mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
+        }
+        bulk_wait_all();
+    }
+}
+
 // Forward FFT along x of independent rows (one component per row), in place.
 template <typename T, int N, int R>
 __global__ void __launch_bounds__(rows_per_cta<N, R>() * (N / R))
@@ -295,6 +423,18 @@ cudaError_t colpass_n(const PassArgs<T>& a, cudaStream_t s) {
     const size_t smem = (size_t)tw_off<T>(COLS * smem_ld_cols<T>(N, COLS)) * sizeof(cplx<T>) +
                         FftPlan<N, R>::tw_size() * sizeof(twel<T>);
     return launch_with_smem(k_colpass<T, N, R, COLS, FWD_ONLY>, (int)grid, COLS * (N / R), smem, s, &a);
+}
+
+template <typename T, int N, bool FWD_ONLY, bool ZPASS>
+cudaError_t colpass_tma_n(const CUtensorMap& map, const ColTmaArgs<T>& a, int grid, cudaStream_t s) {
+    constexpr int R = Tune<T>::kColR(N);
+    constexpr int COLS = Tune<T>::kColCols(N);
+    const size_t smem = colpass_tma_smem<T, N, COLS>(R) + FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
+    auto kern = k_colpass_tma<T, N, R, COLS, FWD_ONLY, ZPASS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, COLS * (N / R), smem, s>>>(map, a);
+    return cudaGetLastError();
 }
 
 template <typename T, int N>
