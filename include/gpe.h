@@ -131,11 +131,31 @@ gpe_status gpe_bin_counts(const gpe_batch* batch, int64_t* counts);
 int64_t gpe_batch_get_step(const gpe_batch* batch);
 gpe_status gpe_batch_set_step(gpe_batch* batch, int64_t step);
 
+/* Reverse-mode step (vector-Jacobian product of one Strang step, Sec. 2.2 scheme; the
+ * paper itself has no adjoint).  With psi_step_in = psi_n, the fields at the start of
+ * step n = step_index (contiguous [ntraj][3][sites] complex, caller-owned device memory,
+ * the batch's layout), and lam = dL/dpsi_{n+1} on entry, lam holds dL/dpsi_n on return
+ * (same layout; gradients in the convention dL/dRe + i dL/dIm).  dL/dq_n, reduced in
+ * FP64 in a fixed order, is added to dLdq (device, max(1, n_knots) doubles) with the
+ * linear interpolation weights of q at t_n + dt/2 (dLdq[0] for constant q).  The first
+ * call allocates the handle's adjoint workspace.  Errors: GPE_EINVAL, GPE_EUNSUPPORTED
+ * (more than one shape, or x extent > 1024). */
+gpe_status gpe_adjoint_step(gpe_batch* batch, const void* psi_step_in, void* lam, int64_t step_index,
+                            double* dLdq, void* stream);
+
+/* Late-time spin structure factor loss over a band of wave numbers:
+ * loss[0] = (1/ntraj) sum_traj sum_{grid modes with kmin <= |k| <= kmax} S_perp(k) of
+ * the fields psi (contiguous [ntraj][3][sites]; S_perp as in observables_accumulate),
+ * FP64, deterministic.  If lam_out is not NULL it receives dloss/dpsi (same layout).
+ * Errors: GPE_EINVAL, GPE_EUNSUPPORTED (as gpe_adjoint_step). */
+gpe_status gpe_sf_band_loss(gpe_batch* batch, const void* psi, double kmin, double kmax, double* loss,
+                            void* lam_out, void* stream);
+
 /* Measurement: when enabled, every launch the batch makes is bracketed by CUDA events on
  * its stream, summed per kernel class: 0 = x pass (local step fused with the x kinetic
  * pass), 1 = strided kinetic pass (y or z), 2 = resident 1D kernel, 3 = noise,
- * 4 = observables (whole pipeline of one call).  gpe_profile_read synchronises the
- * device, writes the summed milliseconds and launch counts of each class (arrays of 5,
+ * 4 = observables (whole pipeline of one call), 5 = adjoint step.  gpe_profile_read synchronises the
+ * device, writes the summed milliseconds and launch counts of each class (arrays of 6,
  * host) since the last read, and resets them. */
 gpe_status gpe_profile_enable(gpe_batch* batch, int32_t enable);
 gpe_status gpe_profile_read(gpe_batch* batch, double* ms, int64_t* launches);

@@ -57,6 +57,8 @@ def _load():
         "gpe_sync_status": ([vp, vp], ctypes.c_int),
         "gpe_profile_enable": ([vp, i32], ctypes.c_int),
         "gpe_profile_read": ([vp, pd, ctypes.POINTER(i64)], ctypes.c_int),
+        "gpe_adjoint_step": ([vp, vp, vp, i64, vp, vp], ctypes.c_int),
+        "gpe_sf_band_loss": ([vp, vp, dbl, dbl, vp, vp, vp], ctypes.c_int),
         "gpe_launch_count": ([], i64),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_diagnostics_noalloc": ([vp, i32, i32, ctypes.POINTER(i32), dbl, ctypes.c_int, dbl, dbl, dbl, vp, vp],
@@ -143,7 +145,7 @@ def gpe_sync_status(h, stream=None):
     return LIB.gpe_sync_status(h, _stream(stream))
 
 
-PROFILE_KINDS = ("xpass", "strided_pass", "resident1d", "noise", "observables")
+PROFILE_KINDS = ("xpass", "strided_pass", "resident1d", "noise", "observables", "adjoint")
 
 
 def gpe_profile_enable(h, on=True):
@@ -151,10 +153,27 @@ def gpe_profile_enable(h, on=True):
 
 
 def gpe_profile_read(h):
-    ms = (ctypes.c_double * 5)()
-    n = (ctypes.c_int64 * 5)()
+    ms = (ctypes.c_double * 6)()
+    n = (ctypes.c_int64 * 6)()
     _check(LIB.gpe_profile_read(h, ms, n))
     return {k: (ms[i], n[i]) for i, k in enumerate(PROFILE_KINDS)}
+
+
+def gpe_adjoint_step(h, psi_step_in, lam, step_index, dLdq, stream=None):
+    """psi_step_in, lam: contiguous (ntraj, 3, *shape) complex CUDA tensors; dLdq: float64 CUDA."""
+    for t in (psi_step_in, lam):
+        assert t.is_cuda and t.is_contiguous()
+    assert dLdq.dtype == torch.float64 and dLdq.is_cuda
+    _check(LIB.gpe_adjoint_step(h, ctypes.c_void_p(psi_step_in.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                                int(step_index), ctypes.c_void_p(dLdq.data_ptr()), _stream(stream)))
+
+
+def gpe_sf_band_loss(h, psi, kmin, kmax, loss, lam_out=None, stream=None):
+    """loss: float64 CUDA tensor (>= 1 element, overwritten); lam_out: like psi or None."""
+    assert psi.is_cuda and psi.is_contiguous() and loss.dtype == torch.float64 and loss.is_cuda
+    lp = ctypes.c_void_p(lam_out.data_ptr()) if lam_out is not None else None
+    _check(LIB.gpe_sf_band_loss(h, ctypes.c_void_p(psi.data_ptr()), float(kmin), float(kmax),
+                                ctypes.c_void_p(loss.data_ptr()), lp, _stream(stream)))
 
 
 def gpe_launch_count():
@@ -249,6 +268,9 @@ class GPEBatch:
     @property
     def step_count(self):
         return LIB.gpe_batch_get_step(self.h)
+
+    def set_step(self, step):
+        _check(LIB.gpe_batch_set_step(self.h, int(step)))
 
 
 def unpack_slot(acc_slot, nbins, ntraj):

@@ -13,6 +13,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "adjoint.h"
 #include "gpe.h"
 #include "internal.h"
 #include "obs.h"
@@ -43,7 +44,7 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 std::atomic<int64_t> g_launches{0};
 
-constexpr int kProfKinds = 5;
+constexpr int kProfKinds = 6;
 
 struct Profiler {
     bool on = false;
@@ -128,6 +129,12 @@ struct gpe_batch {
     std::vector<void*> allocs;
     ObsWork obs;
     Profiler prof;
+    // adjoint / loss workspace (allocated on first use)
+    void* adj_phi = nullptr;        // ntraj x 3 x sites
+    void* adj_W = nullptr;          // ntraj x sites
+    void** adj_ptrs = nullptr;      // 3 x ntraj pointer tables
+    double* adj_part = nullptr;     // partial sums
+    int64_t adj_nparts = 0;
 };
 
 namespace {
@@ -553,6 +560,168 @@ gpe_status gpe_batch_set_step(gpe_batch* b, int64_t step) {
     if (!b || step < 0) return fail(GPE_EINVAL, "bad batch or step");
     b->step = step;
     return GPE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+gpe_status adj_workspace(gpe_batch* b) {
+    if (b->adj_phi) return GPE_OK;
+    const Group& g = b->groups[0];
+    const size_t vb = sizeof(cplx<T>);
+    const int64_t nparts = std::max<int64_t>(adjoint_parts<T>(g), 152 * 8) + 16;
+    gpe_status s;
+    if ((s = dev_alloc(b, &b->adj_phi, vb * 3 * g.sites * g.ntraj)) != GPE_OK) return s;
+    if ((s = dev_alloc(b, &b->adj_W, vb * g.sites * g.ntraj)) != GPE_OK) return s;
+    if ((s = dev_alloc(b, (void**)&b->adj_ptrs, sizeof(void*) * 3 * g.ntraj)) != GPE_OK) return s;
+    if ((s = dev_alloc(b, (void**)&b->adj_part, sizeof(double) * nparts)) != GPE_OK) return s;
+    b->adj_nparts = nparts;
+    return GPE_OK;
+}
+
+template <typename T>
+PassArgs<T> adj_col_args(const gpe_batch* b, const Group& g, int ax, void** ptrs, int ncomp, bool half) {
+    PassArgs<T> a{};
+    a.ptrs = reinterpret_cast<cplx<T>* const*>(ptrs);
+    a.comp_stride = g.sites;
+    a.ntraj = g.ntraj;
+    a.ncomp = ncomp;
+    a.status = b->d_status;
+    for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[ax][ri]);
+    a.ph = reinterpret_cast<const twel<T>*>(half ? g.ph_half[ax] : g.ph_full[ax]);
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    if (ax == 1) {
+        a.stride = nx;
+        a.n_outer = nz;
+        a.outer_stride = (int64_t)nx * ny;
+    } else {
+        a.stride = (int64_t)nx * ny;
+        a.n_outer = ny;
+        a.outer_stride = nx;
+    }
+    a.nx_tiles = nx / colpass_cols<T>(g.n[ax]);
+    return a;
+}
+
+template <typename T>
+AdjArgs<T> adj_x_args(const gpe_batch* b, const Group& g, double q) {
+    AdjArgs<T> a{};
+    a.sites = g.sites;
+    a.rows_per_traj = (int64_t)g.n[1] * g.n[2];
+    a.total_rows = a.rows_per_traj * g.ntraj;
+    for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[0][ri]);
+    a.ph = reinterpret_cast<const twel<T>*>(g.ph_half[0]);
+    a.c0 = (T)b->p.c0;
+    a.c1 = (T)b->p.c1;
+    a.q = (T)q;
+    a.dt = (T)b->p.dt;
+    return a;
+}
+
+template <typename T>
+gpe_status adjoint_step_t(gpe_batch* b, const void* psi_in, void* lam, int64_t step, double* dLdq, cudaStream_t s) {
+    gpe_status st = adj_workspace<T>(b);
+    if (st != GPE_OK) return st;
+    const Group& g = b->groups[0];
+    const size_t vb = sizeof(cplx<T>);
+    const int64_t tstride = (int64_t)vb * 3 * g.sites;
+    GPE_CK(cudaMemcpyAsync(b->adj_phi, psi_in, tstride * g.ntraj, cudaMemcpyDeviceToDevice, s));
+    void** phi_ptrs = b->adj_ptrs;
+    void** lam_ptrs = b->adj_ptrs + g.ntraj;
+    GPE_CK(launch_fill_ptrs(phi_ptrs, b->adj_phi, tstride, g.ntraj, s));
+    GPE_CK(launch_fill_ptrs(lam_ptrs, lam, tstride, g.ntraj, s));
+    const double t_mid = ((double)step + 0.5) * b->p.dt;
+    const double q = q_at_host(b, t_mid);
+    g_launches += 4 + 4 * (g.ndim - 1) + 1;
+    // phi = K(dt/2) psi_n
+    for (int ax = 1; ax < g.ndim; ++ax)
+        GPE_CK(launch_colpass_mode<T>(g.n[ax], 0, adj_col_args<T>(b, g, ax, phi_ptrs, 3, true), s));
+    const AdjArgs<T> xa = adj_x_args<T>(b, g, q);
+    GPE_CK(launch_xkin<T>(g.n[0], xa, reinterpret_cast<cplx<T>*>(b->adj_phi), false, s));
+    // lam <- K(-dt/2) L^T K(-dt/2) lam
+    for (int ax = 1; ax < g.ndim; ++ax)
+        GPE_CK(launch_colpass_mode<T>(g.n[ax], 2, adj_col_args<T>(b, g, ax, lam_ptrs, 3, true), s));
+    int nparts = 0;
+    GPE_CK(launch_xadj<T>(g.n[0], xa, reinterpret_cast<cplx<T>*>(lam), reinterpret_cast<const cplx<T>*>(b->adj_phi),
+                          b->adj_part, &nparts, s));
+    GPE_CK(launch_dq_final(b->adj_part, nparts, t_mid, b->p.n_knots, b->p.t_end, dLdq, s));
+    for (int ax = 1; ax < g.ndim; ++ax)
+        GPE_CK(launch_colpass_mode<T>(g.n[ax], 2, adj_col_args<T>(b, g, ax, lam_ptrs, 3, true), s));
+    return GPE_OK;
+}
+
+template <typename T>
+gpe_status sf_loss_t(gpe_batch* b, const void* psi, double kmin, double kmax, double* loss, void* lam_out,
+                     cudaStream_t s) {
+    gpe_status st = adj_workspace<T>(b);
+    if (st != GPE_OK) return st;
+    const Group& g = b->groups[0];
+    const size_t vb = sizeof(cplx<T>);
+    const int64_t total = g.sites * g.ntraj;
+    cplx<T>* W = reinterpret_cast<cplx<T>*>(b->adj_W);
+    void** w_ptrs = b->adj_ptrs + 2 * g.ntraj;
+    GPE_CK(launch_fill_ptrs(w_ptrs, b->adj_W, (int64_t)vb * g.sites, g.ntraj, s));
+    GPE_CK(launch_fperp<T>(reinterpret_cast<const cplx<T>*>(psi), W, g.sites, total, s));
+    const twel<T>* twx[3] = {reinterpret_cast<const twel<T>*>(g.tw[0][0]), reinterpret_cast<const twel<T>*>(g.tw[0][1]),
+                             reinterpret_cast<const twel<T>*>(g.tw[0][2])};
+    const int64_t rows = (int64_t)g.ntraj * g.n[1] * g.n[2];
+    GPE_CK(launch_rowfft<T>(g.n[0], W, rows, twx, s, -1));
+    for (int ax = 1; ax < g.ndim; ++ax)
+        GPE_CK(launch_colpass_mode<T>(g.n[ax], 1, adj_col_args<T>(b, g, ax, w_ptrs, 1, true), s));
+    const double c = std::pow(g.dx, g.ndim) / ((double)g.sites * (double)g.ntraj);
+    int nparts = 0;
+    GPE_CK(launch_sf_mask<T>(W, g.sites, total, g.n, g.dx, kmin, kmax, c, b->adj_part, &nparts, s));
+    GPE_CK(launch_sum_final(b->adj_part, nparts, loss, s));
+    g_launches += 4 + (g.ndim - 1);
+    if (lam_out) {
+        for (int ax = 1; ax < g.ndim; ++ax)
+            GPE_CK(launch_colpass_mode<T>(g.n[ax], 3, adj_col_args<T>(b, g, ax, w_ptrs, 1, true), s));
+        GPE_CK(launch_rowfft<T>(g.n[0], W, rows, twx, s, +1));
+        GPE_CK(launch_sf_seed<T>(reinterpret_cast<const cplx<T>*>(psi), W, reinterpret_cast<cplx<T>*>(lam_out),
+                                 g.sites, total, 1.0, s));
+        g_launches += 2 + (g.ndim - 1);
+    }
+    return GPE_OK;
+}
+
+gpe_status adj_check(const gpe_batch* b, const void* p1, const void* p2) {
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    if (b->groups.size() != 1) return fail(GPE_EUNSUPPORTED, "the adjoint needs a batch of one shape");
+    if (b->groups[0].n[0] > 1024) return fail(GPE_EUNSUPPORTED, "the adjoint supports x extents up to 1024");
+    if (!p1 || ((uintptr_t)p1 & 15u)) return fail(GPE_EINVAL, "field pointer NULL or not 16-byte aligned");
+    if (p2 && ((uintptr_t)p2 & 15u)) return fail(GPE_EINVAL, "cotangent pointer not 16-byte aligned");
+    return GPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gpe_status gpe_adjoint_step(gpe_batch* b, const void* psi_step_in, void* lam, int64_t step_index, double* dLdq,
+                            void* stream) {
+    g_err.clear();
+    gpe_status st = adj_check(b, psi_step_in, lam);
+    if (st != GPE_OK) return st;
+    if (!lam || !dLdq) return fail(GPE_EINVAL, "lam and dLdq must be non-NULL");
+    if (step_index < 0) return fail(GPE_EINVAL, "step_index < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    ProfScope ps(b, 5, s, 0);
+    return b->dtype == GPE_C64 ? adjoint_step_t<float>(b, psi_step_in, lam, step_index, dLdq, s)
+                               : adjoint_step_t<double>(b, psi_step_in, lam, step_index, dLdq, s);
+}
+
+gpe_status gpe_sf_band_loss(gpe_batch* b, const void* psi, double kmin, double kmax, double* loss, void* lam_out,
+                            void* stream) {
+    g_err.clear();
+    gpe_status st = adj_check(b, psi, lam_out);
+    if (st != GPE_OK) return st;
+    if (!loss) return fail(GPE_EINVAL, "loss must be non-NULL");
+    if (!(kmax >= kmin)) return fail(GPE_EINVAL, "need kmin <= kmax");
+    cudaStream_t s = (cudaStream_t)stream;
+    return b->dtype == GPE_C64 ? sf_loss_t<float>(b, psi, kmin, kmax, loss, lam_out, s)
+                               : sf_loss_t<double>(b, psi, kmin, kmax, loss, lam_out, s);
 }
 
 gpe_status gpe_profile_enable(gpe_batch* b, int32_t enable) {

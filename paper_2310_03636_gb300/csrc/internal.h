@@ -90,11 +90,16 @@ template <typename T>
 cudaError_t launch_xpass(int n, bool pre, const PassArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_colpass(int n, const PassArgs<T>& a, cudaStream_t s);
+// Column pass in a given mode: 0 kinetic factor, 1 forward FFT only, 2 adjoint kinetic
+// factor (conjugate phases), 3 unnormalised inverse FFT only.
+template <typename T>
+cudaError_t launch_colpass_mode(int n, int mode, const PassArgs<T>& a, cudaStream_t s);
 // Forward transform only (no phase, no inverse): used on spectra workspaces.
 template <typename T>
 cudaError_t launch_colfft(int n, const PassArgs<T>& a, cudaStream_t s);
+// Row FFTs along x, dir = -1 forward, +1 unnormalised inverse.
 template <typename T>
-cudaError_t launch_rowfft(int n, cplx<T>* data, int64_t rows, const twel<T>* const* tw, cudaStream_t s);
+cudaError_t launch_rowfft(int n, cplx<T>* data, int64_t rows, const twel<T>* const* tw, cudaStream_t s, int dir = -1);
 template <typename T>
 int colpass_cols(int n);
 // Persistent TMA column pass over a contiguous group: axis 1 (y) or 2 (z).

@@ -22,11 +22,11 @@ cudaError_t launch_xpass<double>(int n, bool pre, const PassArgs<double>& a, cud
 template <>
 cudaError_t launch_colpass<double>(int n, const PassArgs<double>& a, cudaStream_t s) {
     switch (n) {
-        case 64: return colpass_n<double, 64, false>(a, s);
-        case 128: return colpass_n<double, 128, false>(a, s);
-        case 256: return colpass_n<double, 256, false>(a, s);
-        case 512: return colpass_n<double, 512, false>(a, s);
-        case 1024: return colpass_n<double, 1024, false>(a, s);
+        case 64: return colpass_n<double, 64, kColK>(a, s);
+        case 128: return colpass_n<double, 128, kColK>(a, s);
+        case 256: return colpass_n<double, 256, kColK>(a, s);
+        case 512: return colpass_n<double, 512, kColK>(a, s);
+        case 1024: return colpass_n<double, 1024, kColK>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -34,26 +34,59 @@ cudaError_t launch_colpass<double>(int n, const PassArgs<double>& a, cudaStream_
 template <>
 cudaError_t launch_colfft<double>(int n, const PassArgs<double>& a, cudaStream_t s) {
     switch (n) {
-        case 64: return colpass_n<double, 64, true>(a, s);
-        case 128: return colpass_n<double, 128, true>(a, s);
-        case 256: return colpass_n<double, 256, true>(a, s);
-        case 512: return colpass_n<double, 512, true>(a, s);
-        case 1024: return colpass_n<double, 1024, true>(a, s);
+        case 64: return colpass_n<double, 64, kColFwd>(a, s);
+        case 128: return colpass_n<double, 128, kColFwd>(a, s);
+        case 256: return colpass_n<double, 256, kColFwd>(a, s);
+        case 512: return colpass_n<double, 512, kColFwd>(a, s);
+        case 1024: return colpass_n<double, 1024, kColFwd>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <>
-cudaError_t launch_rowfft<double>(int n, cplx<double>* d, int64_t rows, const twel<double>* const* tw, cudaStream_t s) {
+cudaError_t launch_colpass_mode<double>(int n, int mode, const PassArgs<double>& a, cudaStream_t s) {
+#define GPE_COLMODE(NN)                                              \
+    case NN:                                                         \
+        switch (mode) {                                              \
+            case kColK: return colpass_n<double, NN, kColK>(a, s);         \
+            case kColFwd: return colpass_n<double, NN, kColFwd>(a, s);     \
+            case kColKConj: return colpass_n<double, NN, kColKConj>(a, s); \
+            case kColInv: return colpass_n<double, NN, kColInv>(a, s);     \
+            default: return cudaErrorInvalidValue;                   \
+        }
     switch (n) {
-        case 64: return rowfft_n<double, 64>(d, rows, tw, s);
-        case 128: return rowfft_n<double, 128>(d, rows, tw, s);
-        case 256: return rowfft_n<double, 256>(d, rows, tw, s);
-        case 512: return rowfft_n<double, 512>(d, rows, tw, s);
-        case 1024: return rowfft_n<double, 1024>(d, rows, tw, s);
-        case 2048: return rowfft_n<double, 2048>(d, rows, tw, s);
-        case 4096: return rowfft_n<double, 4096>(d, rows, tw, s);
-        case 8192: return rowfft_n<double, 8192>(d, rows, tw, s);
+        GPE_COLMODE(64)
+        GPE_COLMODE(128)
+        GPE_COLMODE(256)
+        GPE_COLMODE(512)
+        GPE_COLMODE(1024)
+        default: return cudaErrorInvalidValue;
+    }
+#undef GPE_COLMODE
+}
+
+template <>
+cudaError_t launch_rowfft<double>(int n, cplx<double>* d, int64_t rows, const twel<double>* const* tw, cudaStream_t s, int dir) {
+    if (dir > 0) {
+        switch (n) {
+            case 64: return rowfft_n<double, 64, 1>(d, rows, tw, s);
+            case 128: return rowfft_n<double, 128, 1>(d, rows, tw, s);
+            case 256: return rowfft_n<double, 256, 1>(d, rows, tw, s);
+            case 512: return rowfft_n<double, 512, 1>(d, rows, tw, s);
+            case 1024: return rowfft_n<double, 1024, 1>(d, rows, tw, s);
+            case 2048: return rowfft_n<double, 2048, 1>(d, rows, tw, s);
+            case 4096: return rowfft_n<double, 4096, 1>(d, rows, tw, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (n) {
+        case 64: return rowfft_n<double, 64, -1>(d, rows, tw, s);
+        case 128: return rowfft_n<double, 128, -1>(d, rows, tw, s);
+        case 256: return rowfft_n<double, 256, -1>(d, rows, tw, s);
+        case 512: return rowfft_n<double, 512, -1>(d, rows, tw, s);
+        case 1024: return rowfft_n<double, 1024, -1>(d, rows, tw, s);
+        case 2048: return rowfft_n<double, 2048, -1>(d, rows, tw, s);
+        case 4096: return rowfft_n<double, 4096, -1>(d, rows, tw, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -145,10 +145,13 @@ constexpr size_t xpass_smem() {
            FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
 }
 
+// Column-pass modes: the kinetic factor (FFT, x ph, iFFT), a forward FFT only, the
+// adjoint kinetic factor (FFT, x conj(ph), iFFT), an unnormalised inverse FFT only.
+enum ColMode { kColK = 0, kColFwd = 1, kColKConj = 2, kColInv = 3 };
+
 // Column pass: pencils of length N along a strided axis, COLS adjacent x columns per
-// block, one component: FFT, x ph, iFFT (FWD_ONLY: forward FFT only).
-// Block index -> (traj, comp, outer, x tile).
-template <typename T, int N, int R, int COLS, bool FWD_ONLY>
+// block, one component, in mode MODE.  Block index -> (traj, comp, outer, x tile).
+template <typename T, int N, int R, int COLS, int MODE>
 __global__ void __launch_bounds__(COLS * (N / R))
 k_colpass(const PassArgs<T> a) {
     using V = cplx<T>;
@@ -173,10 +176,14 @@ k_colpass(const PassArgs<T> a) {
 #pragma unroll
     for (int m = 0; m < R; ++m) v[0][m] = base[(int64_t)m * TP * a.stride];
     __syncthreads();
-    fft_pencil<N, R, -1, 1, Sync::Block>(v, buf, tws, t);
-    if constexpr (!FWD_ONLY) {
+    if constexpr (MODE == kColInv) {
+        fft_pencil<N, R, +1, 1, Sync::Block>(v, buf, tws, t);
+    } else {
+        fft_pencil<N, R, -1, 1, Sync::Block>(v, buf, tws, t);
+    }
+    if constexpr (MODE == kColK || MODE == kColKConj) {
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[0][m] = twmul<-1>(v[0][m], a.ph[t + m * TP]);
+        for (int m = 0; m < R; ++m) v[0][m] = twmul<MODE == kColK ? -1 : +1>(v[0][m], a.ph[t + m * TP]);
         fft_pencil<N, R, +1, 1, Sync::Block>(v, buf, tws, t);
     }
 #pragma unroll
@@ -309,8 +316,9 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
     }
 }
 
-// Forward FFT along x of independent rows (one component per row), in place.
-template <typename T, int N, int R>
+// FFT along x of independent rows (one component per row), in place: DIR = -1 forward,
+// +1 unnormalised inverse.
+template <typename T, int N, int R, int DIR>
 __global__ void __launch_bounds__(rows_per_cta<N, R>() * (N / R))
 k_rowfft(cplx<T>* __restrict__ data, int64_t rows, const twel<T>* __restrict__ tw) {
     using V = cplx<T>;
@@ -331,7 +339,7 @@ k_rowfft(cplx<T>* __restrict__ data, int64_t rows, const twel<T>* __restrict__ t
 #pragma unroll
     for (int m = 0; m < R; ++m) v[0][m] = valid ? base[m * TP] : mk((T)0, (T)0);
     __syncthreads();
-    fft_pencil<N, R, -1, 1, Sync::Block>(v, buf, tws, t);
+    fft_pencil<N, R, DIR, 1, Sync::Block>(v, buf, tws, t);
     if (valid) {
 #pragma unroll
         for (int m = 0; m < R; ++m) base[m * TP] = v[0][m];
@@ -415,14 +423,14 @@ cudaError_t xpass_n(bool pre, const PassArgs<T>& a, cudaStream_t s) {
     return launch_with_smem(k_xpass<T, N, R, false>, (int)grid, RPC * TP, smem, s, &a);
 }
 
-template <typename T, int N, bool FWD_ONLY>
+template <typename T, int N, int MODE>
 cudaError_t colpass_n(const PassArgs<T>& a, cudaStream_t s) {
     constexpr int R = Tune<T>::kColR(N);
     constexpr int COLS = Tune<T>::kColCols(N);
     const int64_t grid = (int64_t)a.ntraj * a.ncomp * a.n_outer * a.nx_tiles;
     const size_t smem = (size_t)tw_off<T>(COLS * smem_ld_cols<T>(N, COLS)) * sizeof(cplx<T>) +
                         FftPlan<N, R>::tw_size() * sizeof(twel<T>);
-    return launch_with_smem(k_colpass<T, N, R, COLS, FWD_ONLY>, (int)grid, COLS * (N / R), smem, s, &a);
+    return launch_with_smem(k_colpass<T, N, R, COLS, MODE>, (int)grid, COLS * (N / R), smem, s, &a);
 }
 
 template <typename T, int N, bool FWD_ONLY, bool ZPASS>
@@ -437,14 +445,14 @@ cudaError_t colpass_tma_n(const CUtensorMap& map, const ColTmaArgs<T>& a, int gr
     return cudaGetLastError();
 }
 
-template <typename T, int N>
+template <typename T, int N, int DIR>
 cudaError_t rowfft_n(cplx<T>* data, int64_t rows, const twel<T>* const* tw, cudaStream_t s) {
     constexpr int R = Tune<T>::kRowR(N);
     constexpr int TP = N / R;
     constexpr int RPC = rows_per_cta<N, R>();
     const int64_t grid = (rows + RPC - 1) / RPC;
     const size_t smem = (size_t)tw_off<T>(RPC * smem_ld<T>(N)) * sizeof(cplx<T>) + FftPlan<N, R>::tw_size() * sizeof(twel<T>);
-    auto kern = k_rowfft<T, N, R>;
+    auto kern = k_rowfft<T, N, R, DIR>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

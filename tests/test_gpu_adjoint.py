@@ -1,0 +1,145 @@
+"""Adjoint of the split step and the late-time S_perp loss on the GPU against the oracle's
+autograd gradient (FP64) and central finite differences."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import gpe_oracle as O
+from paper_2310_03636_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+C0, C1 = 1.0, -0.1
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2310_03636_gb300 import binding
+    return binding
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+@pytest.mark.parametrize("shape,knots", [((64, 128), None), ((128, 64), [0.2, 0.1, 0.05]), ((128,), [0.3, 0.0]),
+                                         ((64, 64, 64), None)])
+def test_adjoint_step_matches_oracle_vjp(B, shape, knots):
+    """One step's VJP: lam_n = J^T lam_{n+1} and dL/dq, L = Re sum conj(lam) psi_{n+1}."""
+    d = len(shape)
+    ntraj, dt, step = 2, 0.05, 3
+    psi = W.random_field(shape, ntraj, seed=41, scale=0.7)
+    lam = W.random_field(shape, ntraj, seed=42, scale=1.0, mean=(0.1, -0.2, 0.3))
+    q0 = 0.09
+    t_end = 10 * dt
+    # oracle
+    p = torch.as_tensor(psi).requires_grad_(True)
+    if knots is None:
+        qt = torch.tensor(q0, dtype=torch.float64, requires_grad=True)
+        qn = qt
+    else:
+        qt = torch.tensor(knots, dtype=torch.float64, requires_grad=True)
+        qn = O.q_piecewise_linear(qt, t_end)((step + 0.5) * dt)
+    out = O.strang_step(p, dt, C0, C1, qn, 1.0, d)
+    L = (torch.as_tensor(lam).conj() * out).real.sum()
+    gp, gq = torch.autograd.grad(L, (p, qt))
+    # GPU
+    psi_d = torch.as_tensor(psi).cuda().contiguous()
+    lam_d = torch.as_tensor(lam).cuda().contiguous()
+    b = B.GPEBatch(shape, ntraj, "c128", C0, C1, q0, dt, q_knots=knots, t_end=t_end)
+    dq = torch.zeros(len(knots) if knots else 1, dtype=torch.float64, device="cuda")
+    B.gpe_adjoint_step(b.h, psi_d, lam_d, step, dq)
+    assert b.sync_status() == B.GPE_OK
+    assert rel(lam_d.cpu().numpy(), gp.numpy()) < 1e-11
+    assert rel(dq.cpu().numpy(), np.atleast_1d(gq.numpy())) < 1e-10
+    b.close()
+
+
+def test_adjoint_step_fp32(B):
+    shape, ntraj, dt = (64, 64), 2, 0.02
+    psi = W.random_field(shape, ntraj, seed=5, scale=0.7)
+    lam = W.random_field(shape, ntraj, seed=6, scale=1.0)
+    p = torch.as_tensor(psi).requires_grad_(True)
+    qt = torch.tensor(0.09, dtype=torch.float64, requires_grad=True)
+    L = (torch.as_tensor(lam).conj() * O.strang_step(p, dt, C0, C1, qt, 1.0, 2)).real.sum()
+    gp, gq = torch.autograd.grad(L, (p, qt))
+    b = B.GPEBatch(shape, ntraj, "c64", C0, C1, 0.09, dt)
+    psi_d = torch.as_tensor(psi).to(torch.complex64).cuda().contiguous()
+    lam_d = torch.as_tensor(lam).to(torch.complex64).cuda().contiguous()
+    dq = torch.zeros(1, dtype=torch.float64, device="cuda")
+    B.gpe_adjoint_step(b.h, psi_d, lam_d, 0, dq)
+    assert rel(lam_d.cpu().numpy().astype(np.complex128), gp.numpy()) < 1e-5
+    assert abs(float(dq[0]) - float(gq)) < 1e-4 * abs(float(gq))
+    b.close()
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (256,), (64, 64, 64)])
+def test_sf_band_loss_and_seed(B, shape):
+    d = len(shape)
+    dx, kmin, kmax = 1.0, 0.2, 0.4 if d > 1 else 0.6
+    psi = W.random_field(shape, 3, seed=9, scale=0.8)
+    p = torch.as_tensor(psi).requires_grad_(True)
+    L = O.sf_band_loss(p, dx, d, kmin, kmax)
+    (g,) = torch.autograd.grad(L, p)
+    b = B.GPEBatch(shape, 3, "c128", C0, C1, 0.09, 0.02)
+    psi_d = torch.as_tensor(psi).cuda().contiguous()
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam = torch.zeros_like(psi_d)
+    B.gpe_sf_band_loss(b.h, psi_d, kmin, kmax, loss, lam)
+    assert abs(float(loss[0]) - float(L.detach())) < 1e-12 * abs(float(L.detach()))
+    assert rel(lam.cpu().numpy(), g.numpy()) < 1e-11
+    b.close()
+
+
+def _oracle_loss(knots, psi0, shape, dt, nsteps, t_end, kmin, kmax):
+    qf = O.q_piecewise_linear(knots, t_end)
+    p = O.propagate(psi0, dt, nsteps, C0, C1, qf, 1.0, len(shape))
+    return O.sf_band_loss(p, 1.0, len(shape), kmin, kmax)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-8), ("c64", 2e-3)])
+def test_full_gradient_vs_oracle(B, dtype, tol):
+    """SpinSFLoss through checkpoints (every 7 steps of 30) against oracle autograd."""
+    from paper_2310_03636_gb300.adjoint import AdjointConfig, sf_loss
+    shape, ntraj, dt, nsteps = (64, 64), 2, 0.05, 30
+    knots = torch.tensor([0.2, 0.15, 0.08, 0.05], dtype=torch.float64)
+    cfg = AdjointConfig(shape, nsteps, dt, t_end=nsteps * dt, kmin=0.3, kmax=1.1, c0=C0, c1=C1, dtype=dtype,
+                        checkpoint_every=7)
+    psi0 = torch.as_tensor(W.random_field(shape, ntraj, seed=3, scale=0.6))
+    k1 = knots.clone().requires_grad_(True)
+    p1 = psi0.clone().requires_grad_(True)
+    Lo = _oracle_loss(k1, p1, shape, dt, nsteps, cfg.t_end, cfg.kmin, cfg.kmax)
+    gk_o, gp_o = torch.autograd.grad(Lo, (k1, p1))
+    k2 = knots.clone().requires_grad_(True)
+    p2 = psi0.clone().cuda().requires_grad_(True)
+    Lg = sf_loss(k2, p2, cfg)
+    Lg.backward()
+    Lo = float(Lo.detach())
+    assert abs(float(Lg) - Lo) < max(tol, 1e-12) * abs(Lo) * (1 if dtype == "c128" else 10)
+    assert rel(k2.grad.numpy(), gk_o.numpy()) < tol
+    assert rel(p2.grad.cpu().numpy(), gp_o.numpy()) < tol
+
+
+def test_gradient_vs_finite_differences(B):
+    """FP64 GPU gradient w.r.t. two knots against central differences of the GPU forward."""
+    from paper_2310_03636_gb300.adjoint import AdjointConfig, sf_loss
+    shape, ntraj, dt, nsteps = (64, 64), 2, 0.02, 120
+    knots = torch.tensor(W.q_ramp_knots(8), dtype=torch.float64)
+    cfg = AdjointConfig(shape, nsteps, dt, t_end=nsteps * dt, kmin=0.2, kmax=0.4, dtype="c128",
+                        checkpoint_every=32)
+    psi0 = torch.as_tensor(W.random_field(shape, ntraj, seed=17, scale=0.5)).cuda()
+    k = knots.clone().requires_grad_(True)
+    L = sf_loss(k, psi0, cfg)
+    L.backward()
+    for j in (1, 5):
+        h = 1e-5
+        kp = knots.clone(); kp[j] += h
+        km = knots.clone(); km[j] -= h
+        fd = (float(sf_loss(kp, psi0, cfg)) - float(sf_loss(km, psi0, cfg))) / (2 * h)
+        assert abs(fd - float(k.grad[j])) < 1e-5 * max(abs(fd), 1e-3)
