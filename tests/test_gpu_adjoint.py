@@ -143,3 +143,64 @@ def test_gradient_vs_finite_differences(B):
         km = knots.clone(); km[j] -= h
         fd = (float(sf_loss(kp, psi0, cfg)) - float(sf_loss(km, psi0, cfg))) / (2 * h)
         assert abs(fd - float(k.grad[j])) < 1e-5 * max(abs(fd), 1e-3)
+
+
+def test_full_size_adjoint_workload(B):
+    """2D 256^2 x 8 trajectories, 64-knot q ramp 0.2 -> 0.05, checkpoints every 256 steps.
+
+    The gradient of the structure factor after the full 4096 steps (t = 82) is dominated
+    by chaotic amplification of the tangent dynamics (~e^{0.4 t}), so no finite difference
+    can resolve it; at this size the test checks (1) that the full-length gradient runs
+    and is finite in FP32 and FP64, (2) the FP64 gradient against central differences at
+    a 200-step horizon on the full grid, (3) the adjoint identity Re<lam, J v> =
+    Re<J^T lam, v> of one full-size step with J v from a central difference."""
+    from paper_2310_03636_gb300.adjoint import AdjointConfig, sf_loss
+    wl = W.C5_ADJ
+    knots = torch.tensor(W.q_ramp_knots(64), dtype=torch.float64)
+    ntraj = wl.ntraj
+    b = B.GPEBatch(wl.shape, ntraj, "c128", wl.c0, wl.c1, wl.q, wl.dt)
+    b.init_noise(W.SEED_BASE + 5, wl.mean_spinor(), wl.noise_per_mode)
+    psi0 = b.psi.clone()
+    b.close()
+    # (1) full length, both precisions
+    for dtype in ("c128", "c64"):
+        cfg = AdjointConfig(wl.shape, wl.steps, wl.dt, t_end=wl.steps * wl.dt, kmin=0.2, kmax=0.4, c0=wl.c0,
+                            c1=wl.c1, dtype=dtype, checkpoint_every=256)
+        k = knots.clone().requires_grad_(True)
+        p = psi0.clone().requires_grad_(True)
+        L = sf_loss(k, p, cfg)
+        L.backward()
+        assert math.isfinite(float(L))
+        assert torch.isfinite(k.grad).all() and torch.isfinite(torch.view_as_real(p.grad)).all()
+    # (2) short horizon on the full grid
+    n_short = 200
+    cfg = AdjointConfig(wl.shape, n_short, wl.dt, t_end=n_short * wl.dt, kmin=0.2, kmax=0.4, c0=wl.c0, c1=wl.c1,
+                        dtype="c128", checkpoint_every=64)
+    k = knots.clone().requires_grad_(True)
+    L = sf_loss(k, psi0, cfg)
+    L.backward()
+    for j in (10, 50):
+        h = 1e-4
+        kp = knots.clone(); kp[j] += h
+        km = knots.clone(); km[j] -= h
+        fd = (float(sf_loss(kp, psi0, cfg)) - float(sf_loss(km, psi0, cfg))) / (2 * h)
+        g = float(k.grad[j])
+        assert abs(fd - g) < 1e-4 * max(abs(fd), abs(g)), (j, fd, g)
+    # (3) adjoint identity for one full-size step
+    g = torch.Generator(device="cuda").manual_seed(7)
+    v = torch.randn(psi0.shape, dtype=torch.complex128, device="cuda", generator=g)
+    lam = torch.randn(psi0.shape, dtype=torch.complex128, device="cuda", generator=g)
+    hh = 1e-6
+    bp = B.GPEBatch(wl.shape, ntraj, "c128", wl.c0, wl.c1, wl.q, wl.dt, psi=(psi0 + hh * v).contiguous())
+    bp.step(1)
+    bm = B.GPEBatch(wl.shape, ntraj, "c128", wl.c0, wl.c1, wl.q, wl.dt, psi=(psi0 - hh * v).contiguous())
+    bm.step(1)
+    jv = (bp.psi - bm.psi) / (2 * hh)
+    lhs = float((lam.conj() * jv).real.sum())
+    lam_in = lam.clone()
+    dq = torch.zeros(1, dtype=torch.float64, device="cuda")
+    B.gpe_adjoint_step(bp.h, psi0.contiguous(), lam_in, 0, dq)
+    rhs = float((lam_in.conj() * v).real.sum())
+    assert abs(lhs - rhs) < 1e-7 * abs(lhs)
+    bp.close()
+    bm.close()
