@@ -47,8 +47,9 @@ typedef enum {
 typedef enum { GPE_C64 = 0, GPE_C128 = 1 } gpe_dtype;
 
 /* One trajectory.  ndim in {1,2,3}; n[a] = points along axis a (x = 0), each a power
- * of two in [64, 1024] for ndim >= 2 and in [64, 4096] (C64) / [64, 2048] (C128) for
- * ndim = 1; unused axes must be 1.  dx = lattice spacing (all axes).  psi = device
+ * of two in [64, 1024] for ndim >= 2 and in [64, 32768] (C64) / [64, 16384] (C128) for
+ * ndim = 1 (beyond 4096 / 2048 points a 1D trajectory runs on a thread-block cluster;
+ * observables support 1D extents up to 4096); unused axes must be 1.  dx = lattice spacing (all axes).  psi = device
  * pointer to the [3][n2][n1][n0] field (caller-owned, 16-byte aligned). */
 typedef struct {
     int32_t ndim;
@@ -126,6 +127,15 @@ gpe_status gpe_obs_layout(const gpe_batch* batch, int32_t* nbins, int64_t* slot_
 
 /* Number of grid modes in each radial bin (host array of nbins int64). */
 gpe_status gpe_bin_counts(const gpe_batch* batch, int64_t* counts);
+
+/* Graph replay.  When enabled and q is constant (n_knots == 0), the first
+ * gpe_step_batch call with a given nsteps captures its whole kernel sequence (all shape
+ * groups, which run concurrently on internal streams forked from and joined back into
+ * the caller's stream) into a CUDA graph, and later calls with the same nsteps replay it
+ * with one launch.  The capture creates graph resources: make the first call for each
+ * nsteps before any stream capture of your own.  Disabled by default; ignored while
+ * profiling is enabled. */
+gpe_status gpe_batch_set_graph(gpe_batch* batch, int32_t enable);
 
 /* Batch time as a step count (t = step * dt); settable for replaying segments. */
 int64_t gpe_batch_get_step(const gpe_batch* batch);

@@ -60,6 +60,7 @@ def _load():
         "gpe_adjoint_step": ([vp, vp, vp, i64, vp, vp], ctypes.c_int),
         "gpe_sf_band_loss": ([vp, vp, dbl, dbl, vp, vp, vp], ctypes.c_int),
         "gpe_launch_count": ([], i64),
+        "gpe_batch_set_graph": ([vp, i32], ctypes.c_int),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_diagnostics_noalloc": ([vp, i32, i32, ctypes.POINTER(i32), dbl, ctypes.c_int, dbl, dbl, dbl, vp, vp],
                                     ctypes.c_int),
@@ -271,6 +272,9 @@ class GPEBatch:
 
     def set_step(self, step):
         _check(LIB.gpe_batch_set_step(self.h, int(step)))
+
+    def set_graph(self, enable=True):
+        _check(LIB.gpe_batch_set_graph(self.h, 1 if enable else 0))
 
 
 def unpack_slot(acc_slot, nbins, ntraj):

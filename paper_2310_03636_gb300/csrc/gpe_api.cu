@@ -129,6 +129,17 @@ struct gpe_batch {
     std::vector<void*> allocs;
     ObsWork obs;
     Profiler prof;
+    // concurrency across shape groups and CUDA-graph replay of whole step sequences
+    std::vector<cudaStream_t> gstream;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    cudaStream_t cap_stream = nullptr;
+    bool graph_mode = false;
+    struct GraphEntry {
+        cudaGraphExec_t exec;
+        int64_t launches;
+    };
+    std::map<int64_t, GraphEntry> graphs;
     // adjoint / loss workspace (allocated on first use)
     void* adj_phi = nullptr;        // ntraj x 3 x sites
     void* adj_W = nullptr;          // ntraj x sites
@@ -242,14 +253,36 @@ gpe_status build_group_tables(gpe_batch* b, Group& g) {
             GPE_CK(cudaMemcpy(g.tw[a][ri], tw.data(), tb, cudaMemcpyHostToDevice));
         }
     }
+    if (g.ndim == 1 && g.n[0] > resident1d_max_n<T>()) {
+        const int M = res1d_cluster_block<T>();
+        const int C = g.n[0] / M;
+        g.cluster = C;
+        gpe_status s;
+        for (int ri = 0; ri < 3; ++ri) {
+            const std::vector<twel<T>> tw = stage_twiddles_host<T>(M, 4 << ri);
+            const size_t tb = sizeof(twel<T>) * tw.size();
+            if ((s = dev_alloc(b, &g.tw_local[ri], tb)) != GPE_OK) return s;
+            GPE_CK(cudaMemcpy(g.tw_local[ri], tw.data(), tb, cudaMemcpyHostToDevice));
+        }
+        std::vector<twel<T>> wn((size_t)C * M);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int r = 0; r < C; ++r)
+            for (int n = 0; n < M; ++n) {
+                const double ang = two_pi * (double)n * (double)r / (double)g.n[0];
+                wn[(size_t)r * M + n] = tw_entry<T>(std::cos(ang), -std::sin(ang));
+            }
+        if ((s = dev_alloc(b, &g.wn, sizeof(twel<T>) * wn.size())) != GPE_OK) return s;
+        GPE_CK(cudaMemcpy(g.wn, wn.data(), sizeof(twel<T>) * wn.size(), cudaMemcpyHostToDevice));
+    }
     return GPE_OK;
 }
 
 template <typename T>
 gpe_status check_sizes(const gpe_traj& t) {
     if (t.ndim == 1) {
-        if (t.n[0] < 64 || t.n[0] > resident1d_max_n<T>())
-            return fail(GPE_EUNSUPPORTED, "1D size %d outside [64, %d]", t.n[0], resident1d_max_n<T>());
+        const int lim = 8 * res1d_cluster_block<T>();
+        if (t.n[0] < 64 || t.n[0] > lim)
+            return fail(GPE_EUNSUPPORTED, "1D size %d outside [64, %d]", t.n[0], lim);
     } else {
         for (int a = 0; a < t.ndim; ++a) {
             const int lim = (a == 0) ? xpass_max_n<T>() : colpass_max_n<T>();
@@ -354,7 +387,12 @@ gpe_status step_group(gpe_batch* b, const Group& g, int64_t nsteps, cudaStream_t
         a.n_knots = b->p.n_knots;
         a.nsteps = nsteps;
         ProfScope ps(b, 2, s, 1);
-        GPE_CK(launch_resident1d<T>(g.n[0], a, s));
+        if (g.cluster > 0) {
+            const twel<T>* twl = reinterpret_cast<const twel<T>*>(g.tw_local[sizeof(T) == 4 ? 2 : 1]);
+            GPE_CK(launch_res1d_cluster<T>(g.n[0], a, twl, reinterpret_cast<const twel<T>*>(g.wn), s));
+        } else {
+            GPE_CK(launch_resident1d<T>(g.n[0], a, s));
+        }
         return GPE_OK;
     }
     // K(dt/2) along the strided axes first (they commute with the x pass), then per step
@@ -366,6 +404,25 @@ gpe_status step_group(gpe_batch* b, const Group& g, int64_t nsteps, cudaStream_t
         GPE_CK(x_pass<T>(b, g, st == 0, last, q, s));
         for (int ax = 1; ax < g.ndim; ++ax) GPE_CK(col_pass<T>(b, g, ax, last, s));
     }
+    return GPE_OK;
+}
+
+// All groups advance nsteps; with several groups each runs on its own stream, forked
+// from and joined back into ``s``, so small groups overlap large ones.
+gpe_status run_steps(gpe_batch* b, int64_t nsteps, cudaStream_t s) {
+    if (b->groups.size() == 1)
+        return (b->dtype == GPE_C64) ? step_group<float>(b, b->groups[0], nsteps, s)
+                                     : step_group<double>(b, b->groups[0], nsteps, s);
+    GPE_CK(cudaEventRecord(b->ev_fork, s));
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+        cudaStream_t gs = b->gstream[i];
+        GPE_CK(cudaStreamWaitEvent(gs, b->ev_fork, 0));
+        gpe_status st = (b->dtype == GPE_C64) ? step_group<float>(b, b->groups[i], nsteps, gs)
+                                              : step_group<double>(b, b->groups[i], nsteps, gs);
+        if (st != GPE_OK) return st;
+        GPE_CK(cudaEventRecord(b->ev_join[i], gs));
+    }
+    for (size_t i = 0; i < b->groups.size(); ++i) GPE_CK(cudaStreamWaitEvent(s, b->ev_join[i], 0));
     return GPE_OK;
 }
 
@@ -466,6 +523,21 @@ gpe_status gpe_batch_create(const gpe_traj* trajs, int32_t ntraj, gpe_dtype dtyp
         }
         g.contiguous = contiguous;
     }
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(fail(GPE_ECUDA, "stream/event creation"));
+    if (b->groups.size() > 1) {
+        for (size_t i = 0; i < b->groups.size(); ++i) {
+            cudaStream_t gs;
+            cudaEvent_t ev;
+            if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess)
+                return cleanup(fail(GPE_ECUDA, "stream creation"));
+            b->gstream.push_back(gs);
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+                return cleanup(fail(GPE_ECUDA, "event creation"));
+            b->ev_join.push_back(ev);
+        }
+    }
     if ((s = obs_init(b->obs, b->groups, b->dtype == GPE_C128, b->device)) != GPE_OK) {
         g_err = obs_last_error();
         return cleanup(s);
@@ -478,6 +550,11 @@ gpe_status gpe_batch_destroy(gpe_batch* b) {
     if (!b) return GPE_OK;
     cudaDeviceSynchronize();
     obs_free(b->obs);
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.exec);
+    for (cudaStream_t gs : b->gstream) cudaStreamDestroy(gs);
+    for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (cudaEvent_t e : b->prof.pool) cudaEventDestroy(e);
     for (void* p : b->allocs) cudaFree(p);
     delete b;
@@ -516,8 +593,31 @@ gpe_status gpe_step_batch(gpe_batch* b, int64_t nsteps, void* stream) {
     if (nsteps < 0) return fail(GPE_EINVAL, "nsteps < 0");
     if (nsteps == 0) return GPE_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    for (const Group& g : b->groups) {
-        gpe_status st = (b->dtype == GPE_C64) ? step_group<float>(b, g, nsteps, s) : step_group<double>(b, g, nsteps, s);
+    if (b->graph_mode && b->p.n_knots == 0 && !b->prof.on) {
+        auto it = b->graphs.find(nsteps);
+        if (it == b->graphs.end()) {
+            const int64_t before = g_launches.load();
+            GPE_CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+            gpe_status st = run_steps(b, nsteps, b->cap_stream);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(b->cap_stream, &graph);
+            if (st != GPE_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (ec != cudaSuccess) return fail(GPE_ECUDA, "stream capture: %s", cudaGetErrorString(ec));
+            cudaGraphExec_t exec = nullptr;
+            const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) return fail(GPE_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+            const int64_t n = g_launches.load() - before;
+            g_launches -= n;
+            it = b->graphs.emplace(nsteps, gpe_batch::GraphEntry{exec, n}).first;
+        }
+        GPE_CK(cudaGraphLaunch(it->second.exec, s));
+        g_launches += it->second.launches;
+    } else {
+        gpe_status st = run_steps(b, nsteps, s);
         if (st != GPE_OK) return st;
     }
     b->step += nsteps;
@@ -749,6 +849,12 @@ gpe_status gpe_profile_read(gpe_batch* b, double* ms, int64_t* launches) {
 }
 
 int64_t gpe_launch_count(void) { return g_launches.load(); }
+
+gpe_status gpe_batch_set_graph(gpe_batch* b, int32_t enable) {
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    b->graph_mode = enable != 0;
+    return GPE_OK;
+}
 
 gpe_status gpe_sync_status(gpe_batch* b, void* stream) {
     g_err.clear();

@@ -75,6 +75,9 @@ struct Group {
     void* ph_full[3] = {};         // per axis: exp(-i dt k^2/2)/n
     void* ph_half[3] = {};         // per axis: exp(-i dt k^2/4)/n
     bool contiguous = false;       // fields back to back from hptrs[0]: tensor-map passes usable
+    int cluster = 0;               // 1D on a thread-block cluster: blocks per trajectory (0: off)
+    void* tw_local[3] = {};        // cluster 1D: stage twiddles of the per-block length M
+    void* wn = nullptr;            // cluster 1D: W_N^{n r}, r < cluster, n < M
     CUtensorMap map_y{};           // 2D map {2 nx, ntraj 3 nz ny} of the batch (ndim >= 2)
     CUtensorMap map_z{};           // 3D map {2 nx, ny, nz 3 ntraj} (ndim == 3)
 };
@@ -112,5 +115,10 @@ template <typename T>
 cudaError_t launch_resident1d(int n, const Res1DArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_noise(const NoiseArgs& a, cudaStream_t s);
+// Points per block of the cluster-resident 1D kernel, and its launcher (N = C M).
+template <typename T> int res1d_cluster_block();
+template <typename T>
+cudaError_t launch_res1d_cluster(int n, const Res1DArgs<T>& a, const twel<T>* tw_local, const twel<T>* wn,
+                                 cudaStream_t s);
 
 }  // namespace gpe

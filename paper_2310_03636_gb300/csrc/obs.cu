@@ -349,6 +349,11 @@ static gpe_status ensure_workspace(ObsWork& w, const std::vector<Group>& groups)
 
 gpe_status obs_accumulate(ObsWork& w, const std::vector<Group>& groups, bool f64, double c0, double c1, double q,
                           double* acc, uint32_t flags, int slot, int* d_status, cudaStream_t s) {
+    for (const Group& g : groups)
+        if (g.n[0] > 4096) {
+            g_obs_err = "observables support x extents up to 4096";
+            return GPE_EUNSUPPORTED;
+        }
     gpe_status st = ensure_workspace(w, groups);
     if (st != GPE_OK) return st;
     for (const Group& g : groups) {
