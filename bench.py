@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", choices=["2d", "1d", "3d", "ragged", "adjoint"], default="2d",
+                   help="2d: the benchmark workload (default); others print a line for that configuration")
     p.add_argument("--ncu-case", action="store_true",
                    help="small profiling target: the 512^2 x 64 batch (403 MB > L2), 4 steps + observables")
     return p.parse_args()
@@ -358,10 +360,106 @@ def ncu_case():
         sys.exit(1)
 
 
+def run_other(args):
+    """One JSON line for the other workload shapes (device-timed, no e2e/CPU legs)."""
+    from paper_2310_03636_gb300 import binding as B
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    extra = {}
+    if args.workload == "1d":
+        wl = W.C1_1D
+        b = B.GPEBatch(wl.shape, wl.ntraj, wl.dtype, wl.c0, wl.c1, wl.q, wl.dt, dx=wl.dx)
+        per, flags = wl.sample_every, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG
+        su = wl.site_updates_per_step * per
+        name, dtype = wl.name, "f64"
+    elif args.workload == "3d":
+        wl = W.C3_3D[1]
+        b = B.GPEBatch(wl.shape, wl.ntraj, wl.dtype, wl.c0, wl.c1, wl.q, wl.dt, dx=wl.dx)
+        per, flags = wl.sample_every, B.GPE_OBS_DIAG
+        su = wl.site_updates_per_step * per
+        name, dtype = wl.name, "f32"
+    elif args.workload == "ragged":
+        shapes = W.ragged_sizes()
+        b = B.GPEBatch(list(shapes), dtype="c64", c0=1.0, c1=-0.1, q=0.09, dt=0.02)
+        b.set_graph(True)
+        per, flags = 250, 0
+        su = sum(int(np.prod(sh)) for sh in shapes) * 3 * per
+        name, dtype = "ragged_200x1d_1k-16k_32x2d_128-1024_c64", "f32"
+        extra["trajectories"] = len(shapes)
+    else:
+        return run_adjoint(args)
+    nb, sd = b.layout()
+    acc = torch.zeros(max(1, args.warmup + args.steps) * max(sd, 1), dtype=torch.float64, device="cuda")
+    b.init_noise(W.SEED_BASE, (0.0, 0.0, 1.0, 0.0, 0.0, 0.0), 0.5)
+    for k in range(args.warmup):
+        b.step(per)
+        if flags:
+            b.observables(acc, flags, k)
+    torch.cuda.synchronize()
+    l0 = B.gpe_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
+    e0.record(stream)
+    for k in range(args.steps):
+        b.step(per)
+        if flags:
+            b.observables(acc, flags, args.warmup + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    out = {"metric": "site-updates/s", "value": su * args.steps / (ms * 1e-3), "unit": "site-updates/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+           "config": {"workload": name, "steps_per_bench_step": per}, "clocks": clk,
+           "gpu_launches": B.gpe_launch_count() - l0, "status": b.sync_status(), **extra}
+    print(json.dumps(out), flush=True)
+    b.close()
+
+
+def run_adjoint(args):
+    """Gradient of the late-time S_perp band loss w.r.t. 64 q knots and the initial fields:
+    2D 256^2 x 8 trajectories, 4096 steps, checkpoints every 256 (forward + recompute +
+    reverse sweep).  site-updates counted for the forward steps only."""
+    from paper_2310_03636_gb300 import binding as B
+    from paper_2310_03636_gb300.adjoint import AdjointConfig, sf_loss
+    torch.cuda.set_device(0)
+    wl = W.C5_ADJ
+    cfg = AdjointConfig(wl.shape, wl.steps, wl.dt, t_end=wl.steps * wl.dt, kmin=0.2, kmax=0.4, c0=wl.c0, c1=wl.c1,
+                        dtype="c64", checkpoint_every=256)
+    b = B.GPEBatch(wl.shape, wl.ntraj, "c64", wl.c0, wl.c1, wl.q, wl.dt)
+    b.init_noise(W.SEED_BASE + 5, wl.mean_spinor(), wl.noise_per_mode)
+    psi0 = b.psi.clone()
+    b.close()
+    knots = torch.tensor(W.q_ramp_knots(64), dtype=torch.float64)
+
+    def once():
+        k = knots.clone().requires_grad_(True)
+        p = psi0.clone().requires_grad_(True)
+        sf_loss(k, p, cfg).backward()
+    for _ in range(max(1, args.warmup // 3)):
+        once()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n = max(1, args.steps // 10)
+    for _ in range(n):
+        once()
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / n
+    su = wl.site_updates_per_step * wl.steps
+    print(json.dumps({"metric": "site-updates/s (forward steps of one gradient)", "value": su / el,
+                      "unit": "site-updates/s", "n_gpus": 1, "steps": n, "warmup": max(1, args.warmup // 3),
+                      "ms_per_step": el * 1e3, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": wl.name, "knots": 64, "checkpoint_every": 256}}), flush=True)
+
+
 def main():
     args = parse()
     if args.ncu_case:
         ncu_case()
+    elif args.workload != "2d":
+        run_other(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

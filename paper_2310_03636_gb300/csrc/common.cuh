@@ -24,6 +24,9 @@ __host__ __device__ __forceinline__ double2 mk(double a, double b) { return make
 
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk(a.x - b.x, a.y - b.y); }
+// FP32 complex add / subtract as one packed two-lane instruction (sm_100 family).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 template <typename V> __device__ __forceinline__ V cconj(V a) { return mk(a.x, -a.y); }
 // a * b
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {

@@ -107,7 +107,7 @@ cudaError_t launch_colpass_tma<double>(int n, int axis, bool fwd_only, const CUt
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = n_tiles < 2 * sms ? n_tiles : 2 * sms;
+    const int grid = n_tiles < kColCtasPerSm * sms ? n_tiles : kColCtasPerSm * sms;
 #define GPE_COLTMA(NN)                                                                                     \
     case NN: {                                                                                             \
         a.tw = tws[tw_slot<Tune<double>::kColR(NN)>()];                                                        \

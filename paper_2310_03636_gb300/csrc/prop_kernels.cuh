@@ -195,6 +195,9 @@ k_colpass(const PassArgs<T> a) {
 // loads tile i+1 while tile i is transformed, and stores each finished tile back through
 // the same tensor map.  ZPASS: pencils along z of a 3D map {2 nx, ny, nz 3 ntraj};
 // otherwise pencils along y of a 2D map {2 nx, rows}.  FWD_ONLY: forward FFT only.
+// Resident blocks per SM the persistent column pass is launched with.
+constexpr int kColCtasPerSm = 2;
+
 template <typename T>
 struct ColTmaArgs {
     int32_t n_tiles;     // tiles in the whole launch
