@@ -171,6 +171,71 @@ def strang_step(psi, dt, c0, c1, q, dx, d):
     return psi
 
 
+# ----------------------------------------------------------------------------------
+# Alternative local step: exact spin rotation (same Eq. (GPE), different splitting)
+# ----------------------------------------------------------------------------------
+#
+# The interaction part of Eq. (GPE) equals c0 rho + c1 F.f + q f_z^2 applied to psi, with
+# f the spin-1 matrices and F = psi^+ f psi the local spin.  The flow of c0 rho + c1 F.f
+# keeps rho and F fixed, so over a time tau it is exactly
+#   psi <- exp(-i c0 rho tau) exp(-i c1 tau F.f) psi,
+# and for spin 1, (u.f)^3 = u.f for a unit vector u, giving
+#   exp(-i th u.f) = 1 - i sin(th) u.f + (cos(th) - 1) (u.f)^2,  th = c1 tau |F|.
+# The q f_z^2 phase is split symmetrically around it.
+
+def spin_dot_f(F_z, F_p, p1, p0, pm):
+    """(F.f) psi with F.f = [[F_z, F_-/sqrt2, 0], [F_+/sqrt2, 0, F_-/sqrt2], [0, F_+/sqrt2, -F_z]],
+    F_+ = F_x + i F_y, F_- = conj(F_+)."""
+    r2 = math.sqrt(2.0)
+    F_m = F_p.conj()
+    return F_z * p1 + F_m / r2 * p0, F_p / r2 * p1 + F_m / r2 * pm, F_p / r2 * p0 - F_z * pm
+
+
+def rotation_interaction(psi, tau, c0, c1, d):
+    """exp(-i c0 rho tau) exp(-i c1 tau F.f) psi per site (F, rho of the input)."""
+    p1, p0, pm = psi.select(-d - 1, 0), psi.select(-d - 1, 1), psi.select(-d - 1, 2)
+    n1, n0, nm = (p1.abs() ** 2), (p0.abs() ** 2), (pm.abs() ** 2)
+    rho = n1 + n0 + nm
+    F_z = n1 - nm
+    F_p = transverse_spin(psi, d)
+    Fabs2 = F_z ** 2 + F_p.real ** 2 + F_p.imag ** 2
+    zero = Fabs2 == 0
+    Fabs = torch.sqrt(torch.where(zero, torch.ones_like(Fabs2), Fabs2))
+    th = c1 * tau * Fabs
+    g1, g0, gm = spin_dot_f(F_z, F_p, p1, p0, pm)
+    h1, h0, hm = spin_dot_f(F_z, F_p, g1, g0, gm)
+    s = torch.where(zero, torch.zeros_like(th), torch.sin(th) / Fabs)
+    c = torch.where(zero, torch.zeros_like(th), (torch.cos(th) - 1.0) / (Fabs * Fabs))
+    ph = torch.exp(-1j * c0 * tau * rho)
+    out = [ph * (p - 1j * s * g + c * h) for p, g, h in ((p1, g1, h1), (p0, g0, h0), (pm, gm, hm))]
+    return torch.stack(out, dim=-d - 1)
+
+
+def quadratic_zeeman(psi, tau, q, d):
+    """exp(-i q f_z^2 tau): psi_+-1 pick up exp(-i q tau), psi_0 unchanged."""
+    phase = torch.exp(torch.as_tensor(-1j * q * tau, dtype=CDT))
+    return torch.stack([psi.select(-d - 1, 0) * phase, psi.select(-d - 1, 1), psi.select(-d - 1, 2) * phase],
+                       dim=-d - 1)
+
+
+def strang_step_rotation(psi, dt, c0, c1, q, dx, d):
+    """K(dt/2) Q(dt/2) R(dt) Q(dt/2) K(dt/2) with R the exact rotation above and Q the
+    quadratic Zeeman phase."""
+    psi = kinetic(psi, 0.5 * dt, dx, d)
+    psi = quadratic_zeeman(psi, 0.5 * dt, q, d)
+    psi = rotation_interaction(psi, dt, c0, c1, d)
+    psi = quadratic_zeeman(psi, 0.5 * dt, q, d)
+    psi = kinetic(psi, 0.5 * dt, dx, d)
+    return psi
+
+
+def propagate_rotation(psi, dt, nsteps, c0, c1, q, dx, d, t0=0.0):
+    for n in range(nsteps):
+        qn = q(t0 + (n + 0.5) * dt) if callable(q) else q
+        psi = strang_step_rotation(psi, dt, c0, c1, qn, dx, d)
+    return psi
+
+
 def q_piecewise_linear(knots, t_end):
     """q(t): piecewise-linear through knots at t_j = j t_end / (K - 1), clamped outside.
 

@@ -464,3 +464,73 @@ def test_gradient_matches_finite_differences():
             fd = (float(loss_of(knots.detach(), pp)) - float(loss_of(knots.detach(), pm))) / (2 * h)
             an = float(gp[idx].real) if unit == 1.0 else float(gp[idx].imag)
             assert abs(fd - an) < 1e-6 * max(1.0, abs(fd))
+
+
+# ---------------------------------------------------------------- rotation integrator
+
+def test_rotation_operator_is_the_gpe_interaction():
+    """c0 rho + c1 F.f + q f_z^2 applied to psi equals the bracket of Eq. (GPE) without
+    the kinetic term (written here from the equation's matrix)."""
+    g = np.random.default_rng(2)
+    p = g.normal(size=3) + 1j * g.normal(size=3)
+    c0, c1, q = 0.8, -0.3, 0.21
+    p1, p0, pm = p
+    n1, n0, nm = abs(p) ** 2
+    rho = n1 + n0 + nm
+    M = np.array([[-2 * nm, np.conj(pm) * p0, 0], [pm * np.conj(p0), -n0 - q / c1, np.conj(p0) * p1],
+                  [0, p0 * np.conj(p1), -2 * n1]])
+    gpe = (q + (c0 + c1) * rho) * p + c1 * M @ p
+    Fz = n1 - nm
+    Fp = math.sqrt(2) * (np.conj(p1) * p0 + np.conj(p0) * pm)
+    Ff = np.array(O.spin_dot_f(torch.tensor(Fz), torch.tensor(Fp), *[torch.tensor(x) for x in p]))
+    rot = c0 * rho * p + c1 * Ff + q * np.array([p1, 0, pm])
+    np.testing.assert_allclose(rot, gpe, atol=1e-13)
+
+
+def test_rotation_step_is_exact_flow_and_conserves_spin():
+    """The rotation step equals expm of -i tau (c0 rho + c1 F.f) (scipy), keeps F and rho."""
+    g = np.random.default_rng(4)
+    p = g.normal(size=3) + 1j * g.normal(size=3)
+    c0, c1, tau = 0.9, -0.4, 0.7
+    t = torch.as_tensor(p.reshape(3, 1))
+    out = O.rotation_interaction(t, tau, c0, c1, 1).numpy().ravel()
+    n = abs(p) ** 2
+    Fz = n[0] - n[2]
+    Fp = math.sqrt(2) * (np.conj(p[0]) * p[1] + np.conj(p[1]) * p[2])
+    r2 = math.sqrt(2)
+    Ff = np.array([[Fz, np.conj(Fp) / r2, 0], [Fp / r2, 0, np.conj(Fp) / r2], [0, Fp / r2, -Fz]])
+    ref = scipy.linalg.expm(-1j * tau * (c0 * n.sum() * np.eye(3) + c1 * Ff)) @ p
+    np.testing.assert_allclose(out, ref, atol=1e-13)
+    n2 = abs(out) ** 2
+    assert abs(n2.sum() - n.sum()) < 1e-13 and abs((n2[0] - n2[2]) - Fz) < 1e-13
+
+
+def test_rotation_scheme_fz_exact_and_second_order():
+    """F_z is conserved to rounding by the rotation scheme (every factor commutes with the
+    total F_z); the scheme is second order and agrees with the paper's scheme as dt -> 0."""
+    psi = T(W.smooth_random_field((64,), 1, seed=3))
+    c0, c1, q, dx = 1.0, -0.5, 0.09, 1.0
+    out = O.propagate_rotation(psi, 0.05, 40, c0, c1, q, dx, 1)
+    dg0 = O.diagnostics(psi, dx, c0, c1, q, 1)[0]
+    dg1 = O.diagnostics(out, dx, c0, c1, q, 1)[0]
+    assert abs(float((dg1[0] - dg1[2]) - (dg0[0] - dg0[2]))) < 1e-12
+    ref = O.propagate(psi, 1.0 / 512, 512, c0, c1, q, dx, 1)
+    errs = []
+    for nst in (10, 20, 40):
+        o = O.propagate_rotation(psi, 1.0 / nst, nst, c0, c1, q, dx, 1)
+        errs.append(float((o - ref).abs().pow(2).sum().sqrt()))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+def test_rotation_uniform_states():
+    """Uniform ferromagnetic state psi_1 = sqrt(n): exp(-i (q + (c0 + c1) n) t) exactly;
+    uniform polar state: exp(-i c0 n t)."""
+    n, c0, c1, q, dt, steps = 0.8, 1.0, -0.1, 0.09, 0.02, 30
+    psi = np.zeros((3, 16), complex)
+    psi[0] = math.sqrt(n)
+    out = O.propagate_rotation(T(psi), dt, steps, c0, c1, q, 1.0, 1).numpy()
+    np.testing.assert_allclose(out[0], math.sqrt(n) * np.exp(-1j * (q + (c0 + c1) * n) * dt * steps), atol=1e-13)
+    psi = np.zeros((3, 16), complex)
+    psi[1] = math.sqrt(n)
+    out = O.propagate_rotation(T(psi), dt, steps, c0, c1, q, 1.0, 1).numpy()
+    np.testing.assert_allclose(out[1], math.sqrt(n) * np.exp(-1j * c0 * n * dt * steps), atol=1e-13)
