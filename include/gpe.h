@@ -128,6 +128,17 @@ gpe_status gpe_obs_layout(const gpe_batch* batch, int32_t* nbins, int64_t* slot_
 /* Number of grid modes in each radial bin (host array of nbins int64). */
 gpe_status gpe_bin_counts(const gpe_batch* batch, int64_t* counts);
 
+/* Local step of the split step.  GPE_INTEGRATOR_PAPER (default): the paper's diagonal
+ * and predictor-averaged spin-mixing steps, D(dt/2) O(dt) D(dt/2) (Sec. 2.2).
+ * GPE_INTEGRATOR_ROTATION: the same interaction of Eq. (GPE) written as
+ * c0 rho + c1 F.f + q f_z^2 and split as Q(dt/2) R(dt) Q(dt/2), where R is the exact
+ * flow exp(-i c0 rho dt) exp(-i c1 dt F.f) (rho and F are invariant under it) and Q the
+ * quadratic Zeeman phase; it conserves F_z exactly.  The adjoint supports only the
+ * paper's step. */
+#define GPE_INTEGRATOR_PAPER 0
+#define GPE_INTEGRATOR_ROTATION 1
+gpe_status gpe_batch_set_integrator(gpe_batch* batch, int32_t kind);
+
 /* Graph replay.  When enabled and q is constant (n_knots == 0), the first
  * gpe_step_batch call with a given nsteps captures its whole kernel sequence (all shape
  * groups, which run concurrently on internal streams forked from and joined back into

@@ -15,6 +15,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgpe.so"
 GPE_OK, GPE_EINVAL, GPE_ENOMEM, GPE_ECUDA, GPE_ETIMEOUT, GPE_ENONFINITE, GPE_EUNSUPPORTED = range(7)
 GPE_C64, GPE_C128 = 0, 1
 GPE_OBS_SPECTRA, GPE_OBS_DIAG = 1, 2
+GPE_INTEGRATOR_PAPER, GPE_INTEGRATOR_ROTATION = 0, 1
 STATUS_NAMES = {0: "GPE_OK", 1: "GPE_EINVAL", 2: "GPE_ENOMEM", 3: "GPE_ECUDA", 4: "GPE_ETIMEOUT",
                 5: "GPE_ENONFINITE", 6: "GPE_EUNSUPPORTED"}
 
@@ -61,6 +62,7 @@ def _load():
         "gpe_sf_band_loss": ([vp, vp, dbl, dbl, vp, vp, vp], ctypes.c_int),
         "gpe_launch_count": ([], i64),
         "gpe_batch_set_graph": ([vp, i32], ctypes.c_int),
+        "gpe_batch_set_integrator": ([vp, i32], ctypes.c_int),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_diagnostics_noalloc": ([vp, i32, i32, ctypes.POINTER(i32), dbl, ctypes.c_int, dbl, dbl, dbl, vp, vp],
                                     ctypes.c_int),
@@ -272,6 +274,9 @@ class GPEBatch:
 
     def set_step(self, step):
         _check(LIB.gpe_batch_set_step(self.h, int(step)))
+
+    def set_integrator(self, kind):
+        _check(LIB.gpe_batch_set_integrator(self.h, int(kind)))
 
     def set_graph(self, enable=True):
         _check(LIB.gpe_batch_set_graph(self.h, 1 if enable else 0))

@@ -124,6 +124,7 @@ struct gpe_batch {
     std::vector<gpe_traj> trajs;
     std::vector<Group> groups;
     int64_t step = 0;
+    int integrator = 0;               // GPE_INTEGRATOR_PAPER or GPE_INTEGRATOR_ROTATION
     int* d_status = nullptr;
     int device = 0;
     std::vector<void*> allocs;
@@ -317,6 +318,7 @@ PassArgs<T> base_args(const gpe_batch* b, const Group& g) {
     a.coef.c1 = (T)b->p.c1;
     a.coef.dt = (T)b->p.dt;
     a.coef.q = (T)b->p.q;
+    a.coef.kind = b->integrator;
     return a;
 }
 
@@ -386,6 +388,7 @@ gpe_status step_group(gpe_batch* b, const Group& g, int64_t nsteps, cudaStream_t
         a.knots = b->d_knots;
         a.n_knots = b->p.n_knots;
         a.nsteps = nsteps;
+        a.kind = b->integrator;
         ProfScope ps(b, 2, s, 1);
         if (g.cluster > 0) {
             const twel<T>* twl = reinterpret_cast<const twel<T>*>(g.tw_local[sizeof(T) == 4 ? 2 : 1]);
@@ -805,6 +808,7 @@ gpe_status gpe_adjoint_step(gpe_batch* b, const void* psi_step_in, void* lam, in
     gpe_status st = adj_check(b, psi_step_in, lam);
     if (st != GPE_OK) return st;
     if (!lam || !dLdq) return fail(GPE_EINVAL, "lam and dLdq must be non-NULL");
+    if (b->integrator != GPE_INTEGRATOR_PAPER) return fail(GPE_EUNSUPPORTED, "the adjoint is written for the paper's local step");
     if (step_index < 0) return fail(GPE_EINVAL, "step_index < 0");
     cudaStream_t s = (cudaStream_t)stream;
     ProfScope ps(b, 5, s, 0);
@@ -849,6 +853,17 @@ gpe_status gpe_profile_read(gpe_batch* b, double* ms, int64_t* launches) {
 }
 
 int64_t gpe_launch_count(void) { return g_launches.load(); }
+
+gpe_status gpe_batch_set_integrator(gpe_batch* b, int32_t kind) {
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    if (kind != GPE_INTEGRATOR_PAPER && kind != GPE_INTEGRATOR_ROTATION) return fail(GPE_EINVAL, "unknown integrator %d", kind);
+    if (kind != b->integrator) {
+        for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.exec);
+        b->graphs.clear();
+    }
+    b->integrator = kind;
+    return GPE_OK;
+}
 
 gpe_status gpe_batch_set_graph(gpe_batch* b, int32_t enable) {
     if (!b) return fail(GPE_EINVAL, "batch is NULL");

@@ -48,6 +48,7 @@ struct Res1DArgs {
     const double* knots;      // device, may be null
     int32_t n_knots;
     int64_t nsteps;
+    int32_t kind;             // local step: 0 paper scheme, 1 spin rotation
 };
 
 struct NoiseArgs {

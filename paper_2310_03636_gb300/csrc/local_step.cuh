@@ -25,6 +25,7 @@ namespace gpe {
 template <typename T>
 struct LocalCoef {
     T c0, c1, q, dt;
+    int kind;   // 0: the paper's D O D step, 1: exact spin rotation (see local_step_rot)
 };
 
 template <typename T, typename V>
@@ -170,8 +171,72 @@ __device__ __forceinline__ void local_step_fast(float2& p1, float2& p0, float2& 
     p0 = rot_minus(p0, gg);
 }
 
+// Alternative local step with the same operator split differently: the interaction part
+// of Eq. (GPE) is c0 rho + c1 F.f + q f_z^2 (f: spin-1 matrices, F = psi^+ f psi).  The
+// flow of c0 rho + c1 F.f keeps rho and F fixed, so it is exactly
+// exp(-i c0 rho tau) exp(-i c1 tau F.f); for spin 1, with th = c1 tau |F|,
+//   exp(-i c1 tau F.f) = 1 - i c1 tau s1(th) F.f - (c1 tau)^2 s2(th) (F.f)^2,
+// s1 = sin(th)/th, s2 = (1 - cos th)/th^2 as power series in th^2 (no division).  The
+// q f_z^2 phase is split symmetrically around it: Q(dt/2) R(dt) Q(dt/2).  F_z is kept
+// exactly by every factor.
+template <typename T, typename V>
+__device__ __forceinline__ void local_step_rot(V& p1, V& p0, V& pm, const LocalCoef<T>& k) {
+    T sq, cq;
+    sincos_t(k.q * (T)0.5 * k.dt, &sq, &cq);
+    p1 = mk(p1.x * cq + p1.y * sq, p1.y * cq - p1.x * sq);
+    pm = mk(pm.x * cq + pm.y * sq, pm.y * cq - pm.x * sq);
+    const T n1 = cabs2(p1), n0 = cabs2(p0), nm = cabs2(pm);
+    const T rho = n1 + n0 + nm, fz = n1 - nm;
+    const V A = cadd(cmulc(p1, p0), cmulc(p0, pm));   // F_+ / sqrt2
+    const T eps = k.c1 * k.dt;
+    const T u = eps * eps * (fz * fz + (T)2 * cabs2(A));
+    T s1, s2;
+    if (u <= (T)0.25) {
+        s1 = (T)2.75573192239858907e-6;
+        s1 = s1 * u + (T)(-1.98412698412698413e-4);
+        s1 = s1 * u + (T)8.33333333333333333e-3;
+        s1 = s1 * u + (T)(-1.66666666666666667e-1);
+        s1 = s1 * u + (T)1;
+        s2 = (T)2.75573192239858907e-7;
+        s2 = s2 * u + (T)(-2.48015873015873016e-5);
+        s2 = s2 * u + (T)1.38888888888888889e-3;
+        s2 = s2 * u + (T)(-4.16666666666666667e-2);
+        s2 = s2 * u + (T)0.5;
+    }
+    if (u > (T)0.25 || (sizeof(T) == 8 && u > (T)1e-6)) {
+        // trigonometric form from the half angle: sin th = 2 sh ch, 1 - cos th = 2 sh^2
+        const T th = sqrt_t(u);
+        T sh, ch;
+        sincos_t((T)0.5 * th, &sh, &ch);
+        s1 = (T)2 * sh * ch / th;
+        s2 = (T)2 * sh * sh / u;
+    }
+    const T e1 = eps * s1, e2 = eps * eps * s2;
+    // g = (F.f) p, w = (F.f) g with F.f = [[fz, A*, 0], [A, 0, A*], [0, A, -fz]]
+    const V g1 = cadd(cscale(p1, fz), cmulc(A, p0));
+    const V g0 = cadd(cmul(A, p1), cmulc(A, pm));
+    const V gm = csub(cmul(A, p0), cscale(pm, fz));
+    const V w1 = cadd(cscale(g1, fz), cmulc(A, g0));
+    const V w0 = cadd(cmul(A, g1), cmulc(A, gm));
+    const V wm = csub(cmul(A, g0), cscale(gm, fz));
+    T sr, cr;
+    sincos_t(k.c0 * rho * k.dt, &sr, &cr);
+    V r1 = mk(p1.x + e1 * g1.y - e2 * w1.x, p1.y - e1 * g1.x - e2 * w1.y);
+    V r0 = mk(p0.x + e1 * g0.y - e2 * w0.x, p0.y - e1 * g0.x - e2 * w0.y);
+    V rm = mk(pm.x + e1 * gm.y - e2 * wm.x, pm.y - e1 * gm.x - e2 * wm.y);
+    // c0 phase on all three, second half of the q phase on m = +-1
+    const T c1x = cr * cq - sr * sq, s1x = sr * cq + cr * sq;   // exp(-i(c0 rho dt + q dt/2))
+    p1 = mk(r1.x * c1x + r1.y * s1x, r1.y * c1x - r1.x * s1x);
+    p0 = mk(r0.x * cr + r0.y * sr, r0.y * cr - r0.x * sr);
+    pm = mk(rm.x * c1x + rm.y * s1x, rm.y * c1x - rm.x * s1x);
+}
+
 template <typename T, typename V>
 __device__ __forceinline__ void local_step(V& p1, V& p0, V& pm, const LocalCoef<T>& k) {
+    if (k.kind == 1) {
+        local_step_rot<T>(p1, p0, pm, k);
+        return;
+    }
     if constexpr (sizeof(T) == 4) {
         local_step_fast(p1, p0, pm, k);
     } else {

@@ -381,7 +381,7 @@ k_resident1d(const Res1DArgs<T> a) {
         for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
     }
     fft_pencil<N, R, +1, 3, SY>(v, buf, tws, t);
-    LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt};
+    LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
 #pragma unroll

@@ -106,7 +106,7 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
     };
 
     kinetic(a.ph_half);
-    LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt};
+    LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
 #pragma unroll

@@ -360,3 +360,28 @@ def test_ragged_graph_replay(B):
     for i, s in enumerate(shapes):
         ref = run_oracle(oracle_initial(s, 1, 71, ids=[i]), 0.02, 60, len(s))
         assert rel_l2_per_comp(outs[1][i].numpy()[None].astype(np.complex128), ref) <= 1e-4
+
+
+@pytest.mark.parametrize("dtype,shape,ntraj,steps,tol", [("c128", (256,), 2, 200, 1e-11), ("c128", (64, 128), 2, 100, 1e-11),
+                                                          ("c128", (8192,), 1, 40, 1e-11), ("c64", (128, 128), 2, 200, 1e-4),
+                                                          ("c128", (64, 64, 64), 1, 10, 1e-11)])
+def test_rotation_integrator(B, dtype, shape, ntraj, steps, tol):
+    """Spin-rotation local step against the oracle's rotation scheme; F_z conserved."""
+    seed, dt = 21, 0.02
+    b = B.GPEBatch(shape, ntraj, dtype, C0, C1, Q, dt)
+    b.set_integrator(B.GPE_INTEGRATOR_ROTATION)
+    b.init_noise(seed, MEAN, 0.5)
+    psi0 = b.psi.cpu().numpy() if b.uniform else None
+    b.step(steps)
+    gpu = b.psi.cpu().numpy().astype(np.complex128)
+    ref = O.propagate_rotation(torch.as_tensor(oracle_initial(shape, ntraj, seed)), dt, steps, C0, C1, Q, 1.0,
+                               len(shape)).numpy()
+    assert rel_l2_per_comp(gpu, ref) <= tol
+    d = len(shape)
+    ax = tuple(range(1, 1 + d))
+    n0 = np.abs(psi0.astype(np.complex128)) ** 2
+    n1 = np.abs(gpu) ** 2
+    fz0 = (n0[:, 0] - n0[:, 2]).sum(axis=ax)
+    fz1 = (n1[:, 0] - n1[:, 2]).sum(axis=ax)
+    assert np.abs(fz1 - fz0).max() <= (1e-10 if dtype == "c128" else 1e-4) * np.abs(n0).sum()
+    b.close()
