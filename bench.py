@@ -223,8 +223,10 @@ def run_ours(args):
     ws, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    seed = W.SEED_BASE + 1000003 * rank
+    from paper_2310_03636_gb300 import sharding
+    seed = W.SEED_BASE
     b = B.GPEBatch(WL.shape, WL.ntraj, "c64", WL.c0, WL.c1, WL.q, WL.dt, dx=WL.dx)
+    b.set_traj_base(sharding.trajectory_base(rank, WL.ntraj))
     nb, sd = b.layout()
     nslots = args.warmup + args.steps
     acc = torch.zeros(nslots * sd, dtype=torch.float64, device=dev)
@@ -261,10 +263,8 @@ def run_ours(args):
     status = b.sync_status()
     value = su_per_step * args.steps * ws / (ms * 1e-3)
 
-    # ensemble exchange: sum the FP64 accumulators over ranks
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(acc, op=dist.ReduceOp.SUM)
+    # ensemble exchange: sum the FP64 spectra accumulators over ranks
+    sharding.reduce_accumulators(acc, ws)
 
     # roofline of the dominant kernel class (bytes per launch: read + write of the 3-component field)
     peak, peak_kind = measured_peaks()

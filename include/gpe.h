@@ -87,8 +87,8 @@ gpe_status gpe_batch_destroy(gpe_batch* batch);
  * mean_spinor = (re, im) of (psi_1, psi_0, psi_-1) and eta complex Gaussian,
  * <|eta|^2> = noise_per_mode / dx^d (noise_per_mode particles per plane-wave mode).
  * eta comes from Philox4x32-10 (Salmon et al., SC'11) keyed by the seed, counter
- * (site mod 2^32, m, trajectory index in the batch, site >> 32), and Box-Muller in
- * FP64.  Resets the batch time to t = 0.  Errors: GPE_EINVAL (NULL mean_spinor,
+ * (site mod 2^32, m, trajectory base + index in the batch, site >> 32), and Box-Muller
+ * in FP64.  Resets the batch time to t = 0.  Errors: GPE_EINVAL (NULL mean_spinor,
  * noise_per_mode < 0). */
 gpe_status tw_init_noise(gpe_batch* batch, uint64_t seed, const double mean_spinor[6],
                          double noise_per_mode, void* stream);
@@ -127,6 +127,12 @@ gpe_status gpe_obs_layout(const gpe_batch* batch, int32_t* nbins, int64_t* slot_
 
 /* Number of grid modes in each radial bin (host array of nbins int64). */
 gpe_status gpe_bin_counts(const gpe_batch* batch, int64_t* counts);
+
+/* Offset added to the batch's trajectory indices in the noise counter (default 0), so
+ * that batches on several devices draw disjoint members of one ensemble: a batch with
+ * base b and n trajectories draws exactly trajectories b .. b+n-1 of a single large
+ * batch with the same seed. */
+gpe_status gpe_batch_set_traj_base(gpe_batch* batch, int64_t base);
 
 /* Local step of the split step.  GPE_INTEGRATOR_PAPER (default): the paper's diagonal
  * and predictor-averaged spin-mixing steps, D(dt/2) O(dt) D(dt/2) (Sec. 2.2).

@@ -63,6 +63,7 @@ def _load():
         "gpe_launch_count": ([], i64),
         "gpe_batch_set_graph": ([vp, i32], ctypes.c_int),
         "gpe_batch_set_integrator": ([vp, i32], ctypes.c_int),
+        "gpe_batch_set_traj_base": ([vp, i64], ctypes.c_int),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_diagnostics_noalloc": ([vp, i32, i32, ctypes.POINTER(i32), dbl, ctypes.c_int, dbl, dbl, dbl, vp, vp],
                                     ctypes.c_int),
@@ -274,6 +275,9 @@ class GPEBatch:
 
     def set_step(self, step):
         _check(LIB.gpe_batch_set_step(self.h, int(step)))
+
+    def set_traj_base(self, base):
+        _check(LIB.gpe_batch_set_traj_base(self.h, int(base)))
 
     def set_integrator(self, kind):
         _check(LIB.gpe_batch_set_integrator(self.h, int(kind)))

@@ -125,6 +125,7 @@ struct gpe_batch {
     std::vector<Group> groups;
     int64_t step = 0;
     int integrator = 0;               // GPE_INTEGRATOR_PAPER or GPE_INTEGRATOR_ROTATION
+    int64_t traj_base = 0;            // added to batch indices in the noise counter
     int* d_status = nullptr;
     int device = 0;
     std::vector<void*> allocs;
@@ -573,11 +574,13 @@ gpe_status tw_init_noise(gpe_batch* b, uint64_t seed, const double mean_spinor[6
     for (int i = 0; i < 6; ++i)
         if (!std::isfinite(mean_spinor[i])) return fail(GPE_EINVAL, "non-finite mean spinor");
     cudaStream_t s = (cudaStream_t)stream;
+    if (b->traj_base + (int64_t)b->trajs.size() > 0xFFFFFFFFll) return fail(GPE_EINVAL, "trajectory index beyond 32 bits");
     for (const Group& g : b->groups) {
         NoiseArgs a{};
         a.ptrs = g.dptrs;
         a.traj_ids = g.d_ids;
         a.ntraj = g.ntraj;
+        a.traj_base = (uint32_t)b->traj_base;
         a.sites = g.sites;
         a.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
         a.key1 = (uint32_t)(seed >> 32);
@@ -853,6 +856,12 @@ gpe_status gpe_profile_read(gpe_batch* b, double* ms, int64_t* launches) {
 }
 
 int64_t gpe_launch_count(void) { return g_launches.load(); }
+
+gpe_status gpe_batch_set_traj_base(gpe_batch* b, int64_t base) {
+    if (!b || base < 0) return fail(GPE_EINVAL, "bad batch or base");
+    b->traj_base = base;
+    return GPE_OK;
+}
 
 gpe_status gpe_batch_set_integrator(gpe_batch* b, int32_t kind) {
     if (!b) return fail(GPE_EINVAL, "batch is NULL");

@@ -55,6 +55,7 @@ struct NoiseArgs {
     void* const* ptrs;        // per trajectory field pointer
     const int32_t* traj_ids;  // batch index of each trajectory (Philox counter word 2)
     int32_t ntraj;
+    uint32_t traj_base;       // added to the batch index
     int64_t sites;
     uint32_t key0, key1;
     double sigma;             // sqrt(noise_per_mode / dx^d)

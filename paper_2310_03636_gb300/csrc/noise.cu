@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(256) k_noise(const NoiseArgs a) {
         const int comp = (int)(rest % 3);
         const int tl = (int)(rest / 3);
         const u32x4 w = philox4x32_10(
-            u32x4{(uint32_t)(site & 0xFFFFFFFFu), (uint32_t)comp, (uint32_t)a.traj_ids[tl],
+            u32x4{(uint32_t)(site & 0xFFFFFFFFu), (uint32_t)comp, a.traj_base + (uint32_t)a.traj_ids[tl],
                   (uint32_t)((uint64_t)site >> 32)},
             a.key0, a.key1);
         const uint64_t x1 = ((uint64_t)w.y << 32) | w.x;
