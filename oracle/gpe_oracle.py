@@ -24,7 +24,9 @@ Readings of the paper used here (it is silent or garbled on these points):
       unchanged, so it is exact;
   R5  the printed order kinetic -> diagonal -> off-diagonal is symmetrised (Strang):
       K(dt/2) D(dt/2) O(dt) D(dt/2) K(dt/2), with q taken at the step midpoint;
-  R6  V_m = 0 (homogeneous periodic box), hbar = m = 1;
+  R6  hbar = m = 1; the potential V_m(x) of the diagonal step is optional (default 0,
+      the homogeneous periodic box), one real field per component, the same for every
+      trajectory, entering the diagonal step as V_m + f_m;
   R7  normalisations of n_m(k) and S_perp(k), radial bins b = round(|k| / (2 pi / L)).
 """
 import math
@@ -71,13 +73,15 @@ def kinetic(psi, tau, dx, d):
     return torch.fft.ifftn(torch.fft.fftn(psi, dim=_dims(d)) * phase, dim=_dims(d))
 
 
-def diag_phases(psi, c0, c1, q, d):
-    """f_m: the diagonal entries of the operator in square brackets of Eq. (GPE) (V = 0).
+def diag_phases(psi, c0, c1, q, d, V=None):
+    """V_m + f_m: the diagonal entries of the operator in square brackets of Eq. (GPE).
 
     f_1  = q + (c0 + c1) rho + c1 (-2 |psi_-1|^2)
     f_0  = q + (c0 + c1) rho + c1 (-|psi_0|^2 - q / c1) = (c0 + c1) rho - c1 |psi_0|^2
     f_-1 = q + (c0 + c1) rho + c1 (-2 |psi_1|^2)
     (the -q/c1 entry cancels q for m = 0; written without the division so c1 = 0 works).
+    V: optional real potential of shape (3, *shape), V_m(x) as in the diagonal step of
+    Sec. 2.2 (None: V = 0).
     """
     n = psi.real ** 2 + psi.imag ** 2
     n1, n0, nm = n.select(-d - 1, 0), n.select(-d - 1, 1), n.select(-d - 1, 2)
@@ -85,12 +89,13 @@ def diag_phases(psi, c0, c1, q, d):
     f1 = q + (c0 + c1) * rho - 2.0 * c1 * nm
     f0 = (c0 + c1) * rho - c1 * n0
     fm = q + (c0 + c1) * rho - 2.0 * c1 * n1
-    return torch.stack([f1, f0, fm], dim=-d - 1)
+    f = torch.stack([f1, f0, fm], dim=-d - 1)
+    return f if V is None else f + torch.as_tensor(V, dtype=RDT)
 
 
-def diag_step(psi, tau, c0, c1, q, d):
-    """Diagonal interaction part: psi'' = exp{-i f_m tau} psi' (second equation, Sec. 2.2)."""
-    return psi * torch.exp(-1j * tau * diag_phases(psi, c0, c1, q, d))
+def diag_step(psi, tau, c0, c1, q, d, V=None):
+    """Diagonal part: psi'' = exp{-i [V_m + f_m] tau} psi' (second equation, Sec. 2.2)."""
+    return psi * torch.exp(-1j * tau * diag_phases(psi, c0, c1, q, d, V))
 
 
 def offdiag_matrix(a, b, theta_over_lambda, lam2):
@@ -161,12 +166,12 @@ def offdiag_step(psi, tau, c1, d):
     return torch.stack([n1, n0, nm], dim=-d - 1)
 
 
-def strang_step(psi, dt, c0, c1, q, dx, d):
+def strang_step(psi, dt, c0, c1, q, dx, d, V=None):
     """One time step: K(dt/2) D(dt/2) O(dt) D(dt/2) K(dt/2) (reading R5)."""
     psi = kinetic(psi, 0.5 * dt, dx, d)
-    psi = diag_step(psi, 0.5 * dt, c0, c1, q, d)
+    psi = diag_step(psi, 0.5 * dt, c0, c1, q, d, V)
     psi = offdiag_step(psi, dt, c1, d)
-    psi = diag_step(psi, 0.5 * dt, c0, c1, q, d)
+    psi = diag_step(psi, 0.5 * dt, c0, c1, q, d, V)
     psi = kinetic(psi, 0.5 * dt, dx, d)
     return psi
 
@@ -211,28 +216,32 @@ def rotation_interaction(psi, tau, c0, c1, d):
     return torch.stack(out, dim=-d - 1)
 
 
-def quadratic_zeeman(psi, tau, q, d):
-    """exp(-i q f_z^2 tau): psi_+-1 pick up exp(-i q tau), psi_0 unchanged."""
+def quadratic_zeeman(psi, tau, q, d, V=None):
+    """exp(-i (q f_z^2 + V) tau): psi_+-1 pick up exp(-i q tau), psi_0 is unchanged by q;
+    with a potential each psi_m also picks up exp(-i V_m tau)."""
     phase = torch.exp(torch.as_tensor(-1j * q * tau, dtype=CDT))
-    return torch.stack([psi.select(-d - 1, 0) * phase, psi.select(-d - 1, 1), psi.select(-d - 1, 2) * phase],
-                       dim=-d - 1)
+    out = torch.stack([psi.select(-d - 1, 0) * phase, psi.select(-d - 1, 1), psi.select(-d - 1, 2) * phase],
+                      dim=-d - 1)
+    if V is not None:
+        out = out * torch.exp(-1j * tau * torch.as_tensor(V, dtype=RDT))
+    return out
 
 
-def strang_step_rotation(psi, dt, c0, c1, q, dx, d):
+def strang_step_rotation(psi, dt, c0, c1, q, dx, d, V=None):
     """K(dt/2) Q(dt/2) R(dt) Q(dt/2) K(dt/2) with R the exact rotation above and Q the
-    quadratic Zeeman phase."""
+    quadratic Zeeman phase (and the potential, which is diagonal too)."""
     psi = kinetic(psi, 0.5 * dt, dx, d)
-    psi = quadratic_zeeman(psi, 0.5 * dt, q, d)
+    psi = quadratic_zeeman(psi, 0.5 * dt, q, d, V)
     psi = rotation_interaction(psi, dt, c0, c1, d)
-    psi = quadratic_zeeman(psi, 0.5 * dt, q, d)
+    psi = quadratic_zeeman(psi, 0.5 * dt, q, d, V)
     psi = kinetic(psi, 0.5 * dt, dx, d)
     return psi
 
 
-def propagate_rotation(psi, dt, nsteps, c0, c1, q, dx, d, t0=0.0):
+def propagate_rotation(psi, dt, nsteps, c0, c1, q, dx, d, t0=0.0, V=None):
     for n in range(nsteps):
         qn = q(t0 + (n + 0.5) * dt) if callable(q) else q
-        psi = strang_step_rotation(psi, dt, c0, c1, qn, dx, d)
+        psi = strang_step_rotation(psi, dt, c0, c1, qn, dx, d, V)
     return psi
 
 
@@ -259,12 +268,12 @@ def q_piecewise_linear(knots, t_end):
     return q_of_t
 
 
-def propagate(psi, dt, nsteps, c0, c1, q, dx, d, t0=0.0):
+def propagate(psi, dt, nsteps, c0, c1, q, dx, d, t0=0.0, V=None):
     """nsteps Strang steps from time t0.  q: number or callable q(t) evaluated at the
-    step midpoint t0 + (n + 1/2) dt."""
+    step midpoint t0 + (n + 1/2) dt.  V: optional potential (3, *shape)."""
     for n in range(nsteps):
         qn = q(t0 + (n + 0.5) * dt) if callable(q) else q
-        psi = strang_step(psi, dt, c0, c1, qn, dx, d)
+        psi = strang_step(psi, dt, c0, c1, qn, dx, d, V)
     return psi
 
 
@@ -325,14 +334,15 @@ def bin_counts(shape):
     return torch.bincount(b)
 
 
-def diagnostics(psi, dx, c0, c1, q, d):
-    """N_m, and the energy split into kinetic, q, c0 and c1 parts (FP64).
+def diagnostics(psi, dx, c0, c1, q, d, V=None):
+    """N_m, and the energy split into kinetic, q, c0, c1 and potential parts (FP64).
 
     E = dx^d sum_x [ sum_m psi_m^* (-Laplacian/2) psi_m + q (n_1 + n_-1)
-                     + c0/2 rho^2 + c1/2 (F_z^2 + |F_perp|^2) ],
+                     + c0/2 rho^2 + c1/2 (F_z^2 + |F_perp|^2) + sum_m V_m n_m ],
     whose functional derivative d E / d psi_m^* reproduces the bracket of Eq. (GPE);
     the Laplacian is the spectral one (Parseval over the grid modes).
-    Returns a tensor (..., 7): N_1, N_0, N_-1, E_kin, E_q, E_c0, E_c1.
+    Returns a tensor (..., 8): N_1, N_0, N_-1, E_kin, E_q, E_c0, E_c1, E_V (E_V = 0
+    without a potential).
     """
     shape = _spatial_shape(psi, d)
     ntot = math.prod(shape)
@@ -349,7 +359,11 @@ def diagnostics(psi, dx, c0, c1, q, d):
     eq = q * (n1 + nm).sum(dim=sp) * vol
     ec0 = 0.5 * c0 * (rho * rho).sum(dim=sp) * vol
     ec1 = 0.5 * c1 * (fz * fz + fp.real ** 2 + fp.imag ** 2).sum(dim=sp) * vol
-    return torch.cat([N, torch.stack([ekin, eq, ec0, ec1], dim=-1)], dim=-1)
+    if V is None:
+        ev = torch.zeros_like(ec1)
+    else:
+        ev = (torch.as_tensor(V, dtype=RDT) * n).sum(dim=sp).sum(-1) * vol
+    return torch.cat([N, torch.stack([ekin, eq, ec0, ec1, ev], dim=-1)], dim=-1)
 
 
 def sf_band_loss(psi, dx, d, kmin, kmax):

@@ -101,6 +101,21 @@ def smooth_random_field(shape, ntraj, seed, kmax_frac=0.25, amp=0.3, mean=(0.2, 
     return m + f
 
 
+def smooth_potential(shape, seed, amp=0.5, dx=1.0, spread=0.2):
+    """Seeded real test potential V_m(x), shape (3, *shape): a periodic cosine well
+    amp * sum_a (1 - cos(2 pi x_a / L_a)) common to the three components, plus a
+    band-limited random part of relative size ``spread`` that differs per component."""
+    d = len(shape)
+    base = np.zeros(shape)
+    for ax, n in enumerate(shape):
+        x = np.arange(n) * dx
+        view = [1] * d
+        view[ax] = n
+        base = base + (1.0 - np.cos(2 * np.pi * x / (n * dx))).reshape(view)
+    rnd = smooth_random_field(shape, 1, seed, kmax_frac=0.125, amp=1.0, mean=(0.0, 0.0, 0.0))[0].real
+    return amp * (base[None] + spread * rnd)
+
+
 def plane_wave(shape, js, dx=1.0):
     """exp(i k.x) with k_a = 2 pi j_a / (n_a dx); js ordered like shape."""
     d = len(shape)

@@ -323,6 +323,88 @@ def test_energy_functional_generates_gpe():
     np.testing.assert_allclose(lhs.numpy(), np.array(H), atol=1e-12)
 
 
+# ---------------------------------------------------------------- external potential
+
+@pytest.mark.parametrize("rotation", [False, True])
+def test_potential_linear_zeeman_and_uniform_shift(rotation):
+    """V_m = v + p m is a global phase plus a linear Zeeman term; both commute with
+    every part of Eq. (GPE) (the interaction depends on psi only through rho, F_z and
+    F_perp's modulus, and the mixing terms conserve F_z), and the split step is covariant
+    under psi_m -> exp(-i p m t) psi_m, so psi_m(t) = exp(-i (v + p m) t) psi_m^{V=0}(t)."""
+    shape, dx, c0, c1, q, dt, n = (32, 16), 1.0, 1.0, -0.4, 0.07, 0.05, 12
+    psi = T(W.smooth_random_field(shape, 1, seed=17))
+    v, pz = 0.3, -0.45
+    V = np.stack([np.full(shape, v + pz), np.full(shape, v), np.full(shape, v - pz)])
+    prop = O.propagate_rotation if rotation else O.propagate
+    ref = prop(psi, dt, n, c0, c1, q, dx, 2)
+    out = prop(psi, dt, n, c0, c1, q, dx, 2, V=V)
+    ph = np.exp(-1j * (v + pz * np.array([1.0, 0.0, -1.0])) * n * dt).reshape(1, 3, 1, 1)
+    np.testing.assert_allclose(out.numpy(), ref.numpy() * ph, atol=1e-12)
+
+
+def test_potential_linear_limit_converges_to_exact_propagator():
+    """c0 = c1 = q = 0: Eq. (GPE) is the linear Schroedinger equation
+    i d psi_m / dt = (-Laplacian/2 + V_m) psi_m.  On the periodic grid its exact solution is
+    expm(-i H_m t) psi_m with H_m the dense grid Hamiltonian (spectral Laplacian); the
+    split step must converge to it at second order in dt (a wrong sign or a missing half
+    of V in D would leave an O(1) error)."""
+    n, dx, t_end = 48, 0.7, 1.2
+    V = W.smooth_potential((n,), seed=5, amp=0.8, dx=dx)
+    psi = T(W.smooth_random_field((n,), 1, seed=9))
+    k = 2 * np.pi * np.fft.fftfreq(n, dx)
+    F = np.fft.fft(np.eye(n), axis=0)
+    lap_k = F.conj().T @ np.diag(0.5 * k * k) @ F / n            # -Laplacian/2 on the grid
+    exact = np.stack([scipy.linalg.expm(-1j * t_end * (lap_k + np.diag(V[m]))) @ psi.numpy()[0, m]
+                      for m in range(3)])
+    errs = []
+    for nst in (12, 24, 48):
+        out = O.propagate(psi, t_end / nst, nst, 0.0, 0.0, 0.0, dx, 1, V=V).numpy()[0]
+        errs.append(np.sqrt((abs(out - exact) ** 2).sum() / (abs(exact) ** 2).sum()))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+    assert errs[-1] < 1e-3
+
+
+def test_potential_energy_conserved_second_order():
+    """With a potential the conserved energy includes E_V = dx^d sum V_m n_m; the split step
+    conserves the total to O(dt^2), while E_V alone changes by far more (the cloud moves
+    in the well), so a dropped or mis-signed E_V breaks the pin."""
+    n, dx, c0, c1, q = 64, 1.0, 1.0, -0.5, 0.09
+    V = W.smooth_potential((n,), seed=12, amp=0.05)
+    psi = T(W.smooth_random_field((n,), 1, seed=3))
+    dg0 = O.diagnostics(psi, dx, c0, c1, q, 1, V=V)[0]
+    dE, dEV = [], []
+    for nst in (10, 20, 40):
+        dg1 = O.diagnostics(O.propagate(psi, 2.0 / nst, nst, c0, c1, q, dx, 1, V=V), dx, c0, c1, q, 1, V=V)[0]
+        dE.append(abs(float(dg1[3:].sum() - dg0[3:].sum())))
+        dEV.append(abs(float(dg1[7] - dg0[7])))
+    assert 3.0 < dE[0] / dE[1] < 5.0 and 3.0 < dE[1] / dE[2] < 5.0, dE
+    assert dEV[-1] > 20 * dE[-1], (dEV, dE)
+
+
+def test_potential_energy_functional_generates_gpe():
+    """With V: dE/d psi_m^* gains V_m psi_m, the potential term of the bracket in the
+    diagonal step of Sec. 2.2."""
+    shape, dx, c0, c1, q = (12, 10), 0.9, 1.1, -0.3, 0.2
+    V = W.smooth_potential(shape, seed=4, amp=0.7, dx=dx)
+    psi = T(W.random_field(shape, 1, seed=21, scale=0.5)[0]).requires_grad_(True)
+    (g0,) = torch.autograd.grad(O.diagnostics(psi, dx, c0, c1, q, 2)[3:].sum(), psi)
+    (g1,) = torch.autograd.grad(O.diagnostics(psi, dx, c0, c1, q, 2, V=V)[3:].sum(), psi)
+    diff = 0.5 * (g1 - g0) / dx ** 2
+    np.testing.assert_allclose(diff.numpy(), V * psi.detach().numpy(), atol=1e-12)
+
+
+def test_rotation_scheme_with_potential_keeps_fz():
+    """A potential is diagonal in m, so the rotation scheme still conserves F_z to rounding."""
+    shape, dx = (64,), 1.0
+    V = W.smooth_potential(shape, seed=8, amp=0.3)
+    psi = T(W.smooth_random_field(shape, 1, seed=3))
+    out = O.propagate_rotation(psi, 0.05, 40, 1.0, -0.5, 0.09, dx, 1, V=V)
+    d0 = O.diagnostics(psi, dx, 1.0, -0.5, 0.09, 1)[0]
+    d1 = O.diagnostics(out, dx, 1.0, -0.5, 0.09, 1)[0]
+    assert abs(float((d1[0] - d1[2]) - (d0[0] - d0[2]))) < 1e-12
+    assert float((out - O.propagate_rotation(psi, 0.05, 40, 1.0, -0.5, 0.09, dx, 1)).abs().max()) > 1e-3
+
+
 # ---------------------------------------------------------------- observables
 
 def _brute_dft(f, dx):
