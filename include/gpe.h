@@ -10,8 +10,8 @@
  * structure factor S_perp(k)) plus norm / energy diagnostics in FP64.
  *
  * Conventions shared by every entry point:
- *  - hbar = m = 1, no external potential.  Field components are ordered
- *    (psi_1, psi_0, psi_-1).
+ *  - hbar = m = 1; external potential V_m(x) = 0 unless set with
+ *    gpe_batch_set_potential.  Field components are ordered (psi_1, psi_0, psi_-1).
  *  - Field layout of one trajectory: [3][n2][n1][n0] complex numbers, contiguous,
  *    x (n[0]) fastest; complex = interleaved (re, im) float (GPE_C64) or double
  *    (GPE_C128).  The buffer must be 16-byte aligned.
@@ -83,8 +83,9 @@ gpe_status gpe_batch_create(const gpe_traj* trajs, int32_t ntraj, gpe_dtype dtyp
 gpe_status gpe_batch_destroy(gpe_batch* batch);
 
 /* Initial truncated-Wigner state (Sec. 2.2: runs start from slightly fluctuating
- * initial conditions): psi_m(x) = mean_m + eta_m(x) for every trajectory, with
- * mean_spinor = (re, im) of (psi_1, psi_0, psi_-1) and eta complex Gaussian,
+ * initial conditions): psi_m(x) = mean_m [+ mean_field_m(x)] + eta_m(x) for every
+ * trajectory, with mean_spinor = (re, im) of (psi_1, psi_0, psi_-1), the optional
+ * mean field of gpe_batch_set_mean_field, and eta complex Gaussian,
  * <|eta|^2> = noise_per_mode / dx^d (noise_per_mode particles per plane-wave mode).
  * eta comes from Philox4x32-10 (Salmon et al., SC'11) keyed by the seed, counter
  * (site mod 2^32, m, trajectory base + index in the batch, site >> 32), and Box-Muller
@@ -111,8 +112,9 @@ gpe_status gpe_step_batch(gpe_batch* batch, int64_t nsteps, void* stream);
  *   S_perp(k) = |F_perp(k)|^2 / L^d,  F_perp(k) = dx^d sum_x F_perp(x) e^{-ik.x},
  *   F_perp = sqrt(2) (psi_1^* psi_0 + psi_0^* psi_-1)   (Sec. 2.1),
  * with bin b = round(|k| / (2 pi / L)); then [ntraj][8] diagnostics (N_1, N_0, N_-1,
- * E_kin, E_q, E_c0, E_c1, 0), E = dx^d sum_x [psi^*(-Laplacian/2)psi + q (n_1 + n_-1)
- * + c0 rho^2 / 2 + c1 (F_z^2 + |F_perp|^2) / 2] at the current q.  Sums are
+ * E_kin, E_q, E_c0, E_c1, E_V), E = dx^d sum_x [psi^*(-Laplacian/2)psi + q (n_1 + n_-1)
+ * + c0 rho^2 / 2 + c1 (F_z^2 + |F_perp|^2) / 2 + sum_m V_m n_m] at the current q
+ * (E_V = 0 without a potential).  Sums are
  * deterministic (fixed reduction order).  The fields are not modified.  The first call
  * on a batch allocates the handle's spectra workspace (four fields per trajectory, in
  * chunks of at most 1 GiB); make it before capturing a stream.
@@ -133,6 +135,22 @@ gpe_status gpe_bin_counts(const gpe_batch* batch, int64_t* counts);
  * base b and n trajectories draws exactly trajectories b .. b+n-1 of a single large
  * batch with the same seed. */
 gpe_status gpe_batch_set_traj_base(gpe_batch* batch, int64_t base);
+
+/* External potential V_m(x) (Sec. 2.2: the diagonal part of the split step applies
+ * exp(-i [V_m(x_j) + f_m] dt)).  V: caller-owned device array [3][n2][n1][n0] of reals in
+ * the batch's precision (float for GPE_C64, double for GPE_C128), components V_1, V_0,
+ * V_-1; it applies to every trajectory whose grid is n (unused axes 1) and must stay
+ * valid while steps, observables or adjoint steps of the batch run.  V = NULL removes
+ * it.  Both local-step integrators and the adjoint include it, and the diagnostics
+ * record carries E_V = dx^d sum_x sum_m V_m n_m.  Drops cached step graphs.  Errors:
+ * GPE_EINVAL (NULL n, V not aligned to its element size, no trajectory on grid n). */
+gpe_status gpe_batch_set_potential(gpe_batch* batch, const int32_t n[3], const void* V);
+
+/* Non-uniform initial states: mean_field (caller-owned device array [3][n2][n1][n0] of
+ * complex FP64 as (re, im) pairs, 16-byte aligned) is added to the mean spinor by
+ * tw_init_noise for every trajectory whose grid is n; NULL removes it.  It is read
+ * during tw_init_noise only.  Errors: GPE_EINVAL (as gpe_batch_set_potential). */
+gpe_status gpe_batch_set_mean_field(gpe_batch* batch, const int32_t n[3], const double* mean_field);
 
 /* Local step of the split step.  GPE_INTEGRATOR_PAPER (default): the paper's diagonal
  * and predictor-averaged spin-mixing steps, D(dt/2) O(dt) D(dt/2) (Sec. 2.2).

@@ -64,6 +64,8 @@ def _load():
         "gpe_batch_set_graph": ([vp, i32], ctypes.c_int),
         "gpe_batch_set_integrator": ([vp, i32], ctypes.c_int),
         "gpe_batch_set_traj_base": ([vp, i64], ctypes.c_int),
+        "gpe_batch_set_potential": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
+        "gpe_batch_set_mean_field": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_diagnostics_noalloc": ([vp, i32, i32, ctypes.POINTER(i32), dbl, ctypes.c_int, dbl, dbl, dbl, vp, vp],
                                     ctypes.c_int),
@@ -196,6 +198,29 @@ def gpe_diagnostics_noalloc(psi, ndim, c0, c1, q, dx, out, stream=None):
                                        _stream(stream)))
 
 
+def _grid(shape):
+    shape = tuple(shape)
+    return (ctypes.c_int32 * 3)(*(list(reversed(shape)) + [1] * (3 - len(shape))))
+
+
+def gpe_batch_set_potential(h, shape, V):
+    """V: contiguous (3, *shape) real CUDA tensor in the batch's precision, or None."""
+    if V is not None:
+        assert V.is_cuda and V.is_contiguous() and V.dtype in (torch.float32, torch.float64)
+        assert tuple(V.shape) == (3,) + tuple(shape)
+    ptr = ctypes.c_void_p(V.data_ptr()) if V is not None else None
+    _check(LIB.gpe_batch_set_potential(h, _grid(shape), ptr))
+
+
+def gpe_batch_set_mean_field(h, shape, field):
+    """field: contiguous (3, *shape) complex128 CUDA tensor, or None."""
+    if field is not None:
+        assert field.is_cuda and field.is_contiguous() and field.dtype == torch.complex128
+        assert tuple(field.shape) == (3,) + tuple(shape)
+    ptr = ctypes.c_void_p(field.data_ptr()) if field is not None else None
+    _check(LIB.gpe_batch_set_mean_field(h, _grid(shape), ptr))
+
+
 def gpe_check_sincos(x, stream=None):
     """x: float32 CUDA tensor -> (n, 4) tensor: own sin, cos, library sin, cos."""
     assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
@@ -284,6 +309,32 @@ class GPEBatch:
 
     def set_graph(self, enable=True):
         _check(LIB.gpe_batch_set_graph(self.h, 1 if enable else 0))
+
+    def set_potential(self, V, shape=None):
+        """V_m(x) for the trajectories on grid ``shape`` (default: the batch's first shape).
+        V: (3, *shape) tensor (moved to the device in the batch's real precision) or None.
+        The batch keeps a reference while it is set."""
+        shape = tuple(shape) if shape is not None else self.shapes[0]
+        if V is not None:
+            rdt = torch.float32 if self.dtype == GPE_C64 else torch.float64
+            dev = self.psi.device if self.uniform else self.psi[0].device
+            V = torch.as_tensor(V).to(device=dev, dtype=rdt).contiguous()
+        gpe_batch_set_potential(self.h, shape, V)
+        if not hasattr(self, "_pot"):
+            self._pot = {}
+        self._pot[shape] = V
+
+    def set_mean_field(self, field, shape=None):
+        """Mean field added to the mean spinor by init_noise on grid ``shape``:
+        (3, *shape) complex tensor (held as complex128 on the device) or None."""
+        shape = tuple(shape) if shape is not None else self.shapes[0]
+        if field is not None:
+            dev = self.psi.device if self.uniform else self.psi[0].device
+            field = torch.as_tensor(field).to(device=dev, dtype=torch.complex128).contiguous()
+        gpe_batch_set_mean_field(self.h, shape, field)
+        if not hasattr(self, "_mf"):
+            self._mf = {}
+        self._mf[shape] = field
 
 
 def unpack_slot(acc_slot, nbins, ntraj):

@@ -113,7 +113,8 @@ k_xadj(const AdjArgs<T> a, cplx<T>* __restrict__ lam, const cplx<T>* __restrict_
     const bool valid = grow < a.total_rows;
     const int64_t g = valid ? grow : 0;
     const int64_t traj = g / a.rows_per_traj;
-    const int64_t off = traj * 3 * a.sites + (g - traj * a.rows_per_traj) * N + t;
+    const int64_t site0 = (g - traj * a.rows_per_traj) * N + t;
+    const int64_t off = traj * 3 * a.sites + site0;
     V* lbase = lam + off;
     const V* pbase = phi + off;
     V* const buf[3] = {sm + (lrow * 3 + 0) * LD, sm + (lrow * 3 + 1) * LD, sm + (lrow * 3 + 2) * LD};
@@ -131,7 +132,9 @@ k_xadj(const AdjArgs<T> a, cplx<T>* __restrict__ lam, const cplx<T>* __restrict_
                 for (int m = 0; m < R; ++m) {
                     const V p[3] = {pbase[m * TP], pbase[a.sites + m * TP], pbase[2 * a.sites + m * TP]};
                     V gg[3] = {v[0][m], v[1][m], v[2][m]};
-                    dq[0] += (double)local_step_bwd<T>(p, gg, a.c0, a.c1, a.q, a.dt);
+                    const SitePot<T> vp = a.vpot ? site_pot<T>(a.vpot, a.sites, site0 + m * TP)
+                                                 : SitePot<T>{(T)0, (T)0, (T)0};
+                    dq[0] += (double)local_step_bwd<T>(p, gg, a.c0, a.c1, a.q, a.dt, vp);
                     v[0][m] = gg[0];
                     v[1][m] = gg[1];
                     v[2][m] = gg[2];

@@ -25,14 +25,15 @@ template <typename V> __device__ __forceinline__ auto re_cxy(V x, V y) { return 
 // Im(conj(x) y)
 template <typename V> __device__ __forceinline__ auto im_cxy(V x, V y) { return x.x * y.y - x.y * y.x; }
 
-// Diagonal step D(tau) forward: p <- p e^{-i theta(p)}; returns the phases.
+// Diagonal step D(tau) forward: p <- p e^{-i theta(p)}; returns the phases.  The
+// potential vp adds a field-independent part to theta.
 template <typename T, typename V>
-__device__ __forceinline__ void diag_fwd(V (&p)[3], T (&th)[3], T c0, T c1, T q, T tau) {
+__device__ __forceinline__ void diag_fwd(V (&p)[3], T (&th)[3], T c0, T c1, T q, T tau, SitePot<T> vp) {
     const T n1 = cabs2(p[0]), n0 = cabs2(p[1]), nm = cabs2(p[2]);
     const T g = (c0 + c1) * (n1 + n0 + nm);
-    th[0] = (q + g - (T)2 * c1 * nm) * tau;
-    th[1] = (g - c1 * n0) * tau;
-    th[2] = (q + g - (T)2 * c1 * n1) * tau;
+    th[0] = (vp.v1 + q + g - (T)2 * c1 * nm) * tau;
+    th[1] = (vp.v0 + g - c1 * n0) * tau;
+    th[2] = (vp.vm + q + g - (T)2 * c1 * n1) * tau;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         T s, c;
@@ -44,11 +45,12 @@ __device__ __forceinline__ void diag_fwd(V (&p)[3], T (&th)[3], T c0, T c1, T q,
 // Pullback of D(tau) at input p (before the phase) with output p' = p e^{-i theta}.
 // g: in = gradient w.r.t. p', out = gradient w.r.t. p.  Returns dL/dq contribution.
 template <typename T, typename V>
-__device__ __forceinline__ T diag_bwd(const V (&p)[3], V (&g)[3], T c0, T c1, T q, T tau) {
+__device__ __forceinline__ T diag_bwd(const V (&p)[3], V (&g)[3], T c0, T c1, T q, T tau, SitePot<T> vp) {
     const T n1 = cabs2(p[0]), n0 = cabs2(p[1]), nm = cabs2(p[2]);
     const T G = c0 + c1;
     const T g0 = G * (n1 + n0 + nm);
-    const T th[3] = {(q + g0 - (T)2 * c1 * nm) * tau, (g0 - c1 * n0) * tau, (q + g0 - (T)2 * c1 * n1) * tau};
+    const T th[3] = {(vp.v1 + q + g0 - (T)2 * c1 * nm) * tau, (vp.v0 + g0 - c1 * n0) * tau,
+                     (vp.vm + q + g0 - (T)2 * c1 * n1) * tau};
     T w[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -235,16 +237,16 @@ __device__ __forceinline__ void offdiag_fwd(V (&r)[3], T c1, T dt) {
 // Pullback of the whole local step at input p (= the state after the leading half
 // kinetic step).  g: in = gradient w.r.t. L(p), out = gradient w.r.t. p.  Returns dL/dq.
 template <typename T, typename V>
-__device__ __forceinline__ T local_step_bwd(const V (&p)[3], V (&g)[3], T c0, T c1, T q, T dt) {
+__device__ __forceinline__ T local_step_bwd(const V (&p)[3], V (&g)[3], T c0, T c1, T q, T dt, SitePot<T> vp) {
     const T h = (T)0.5 * dt;
     V r[3] = {p[0], p[1], p[2]};
     T th[3];
-    diag_fwd<T>(r, th, c0, c1, q, h);   // r = D(h) p
+    diag_fwd<T>(r, th, c0, c1, q, h, vp);   // r = D(h) p
     V o[3] = {r[0], r[1], r[2]};
-    offdiag_fwd<T>(o, c1, dt);          // o = O r
-    T dq = diag_bwd<T>(o, g, c0, c1, q, h);
+    offdiag_fwd<T>(o, c1, dt);              // o = O r
+    T dq = diag_bwd<T>(o, g, c0, c1, q, h, vp);
     offdiag_bwd<T>(r, g, c1, dt);
-    dq += diag_bwd<T>(p, g, c0, c1, q, h);
+    dq += diag_bwd<T>(p, g, c0, c1, q, h, vp);
     return dq;
 }
 

@@ -13,6 +13,7 @@ struct AdjArgs {
     const twel<T>* tw[3];     // x-axis stage twiddles for R = 4, 8, 16
     const twel<T>* ph;        // x-axis phase table exp(-i dt k^2 / 4) / nx
     T c0, c1, q, dt;
+    const T* vpot;            // potential [3][sites] shared by the trajectories, or null
 };
 
 template <typename T> int64_t adjoint_parts(const Group& g);

@@ -365,6 +365,7 @@ cudaError_t x_pass(gpe_batch* b, const Group& g, bool pre, bool half_post, doubl
     a.rows_per_traj = (int64_t)g.n[1] * g.n[2];
     a.total_rows = a.rows_per_traj * g.ntraj;
     a.coef.q = (T)q;
+    a.vpot = reinterpret_cast<const T*>(g.vpot);
     return launch_xpass<T>(g.n[0], pre, a, s);
 }
 
@@ -390,6 +391,7 @@ gpe_status step_group(gpe_batch* b, const Group& g, int64_t nsteps, cudaStream_t
         a.n_knots = b->p.n_knots;
         a.nsteps = nsteps;
         a.kind = b->integrator;
+        a.vpot = reinterpret_cast<const T*>(g.vpot);
         ProfScope ps(b, 2, s, 1);
         if (g.cluster > 0) {
             const twel<T>* twl = reinterpret_cast<const twel<T>*>(g.tw_local[sizeof(T) == 4 ? 2 : 1]);
@@ -409,6 +411,11 @@ gpe_status step_group(gpe_batch* b, const Group& g, int64_t nsteps, cudaStream_t
         for (int ax = 1; ax < g.ndim; ++ax) GPE_CK(col_pass<T>(b, g, ax, last, s));
     }
     return GPE_OK;
+}
+
+void drop_graphs(gpe_batch* b) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.exec);
+    b->graphs.clear();
 }
 
 // All groups advance nsteps; with several groups each runs on its own stream, forked
@@ -586,6 +593,7 @@ gpe_status tw_init_noise(gpe_batch* b, uint64_t seed, const double mean_spinor[6
         a.key1 = (uint32_t)(seed >> 32);
         a.sigma = std::sqrt(noise_per_mode / std::pow(g.dx, g.ndim));
         for (int i = 0; i < 6; ++i) a.mean[i] = mean_spinor[i];
+        a.mean_field = g.mean_field;
         ProfScope ps(b, 3, s, 1);
         GPE_CK(b->dtype == GPE_C64 ? launch_noise<float>(a, s) : launch_noise<double>(a, s));
     }
@@ -723,6 +731,7 @@ AdjArgs<T> adj_x_args(const gpe_batch* b, const Group& g, double q) {
     a.c1 = (T)b->p.c1;
     a.q = (T)q;
     a.dt = (T)b->p.dt;
+    a.vpot = reinterpret_cast<const T*>(g.vpot);
     return a;
 }
 
@@ -866,11 +875,48 @@ gpe_status gpe_batch_set_traj_base(gpe_batch* b, int64_t base) {
 gpe_status gpe_batch_set_integrator(gpe_batch* b, int32_t kind) {
     if (!b) return fail(GPE_EINVAL, "batch is NULL");
     if (kind != GPE_INTEGRATOR_PAPER && kind != GPE_INTEGRATOR_ROTATION) return fail(GPE_EINVAL, "unknown integrator %d", kind);
-    if (kind != b->integrator) {
-        for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.exec);
-        b->graphs.clear();
-    }
+    if (kind != b->integrator) drop_graphs(b);
     b->integrator = kind;
+    return GPE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Groups whose grid is n (unused axes 1); returns how many matched.
+template <typename F>
+int for_shape(gpe_batch* b, const int32_t n[3], F&& f) {
+    int hits = 0;
+    for (Group& g : b->groups)
+        if (g.n[0] == n[0] && g.n[1] == n[1] && g.n[2] == n[2]) {
+            f(g);
+            ++hits;
+        }
+    return hits;
+}
+
+}  // namespace
+
+extern "C" {
+
+gpe_status gpe_batch_set_potential(gpe_batch* b, const int32_t n[3], const void* V) {
+    g_err.clear();
+    if (!b || !n) return fail(GPE_EINVAL, "batch or n is NULL");
+    const size_t eb = b->dtype == GPE_C64 ? sizeof(float) : sizeof(double);
+    if (V && ((uintptr_t)V % eb)) return fail(GPE_EINVAL, "potential not aligned to its element size");
+    if (for_shape(b, n, [&](Group& g) { g.vpot = V; }) == 0)
+        return fail(GPE_EINVAL, "no trajectories of shape %d x %d x %d", n[0], n[1], n[2]);
+    drop_graphs(b);
+    return GPE_OK;
+}
+
+gpe_status gpe_batch_set_mean_field(gpe_batch* b, const int32_t n[3], const double* mean_field) {
+    g_err.clear();
+    if (!b || !n) return fail(GPE_EINVAL, "batch or n is NULL");
+    if (mean_field && ((uintptr_t)mean_field % 16)) return fail(GPE_EINVAL, "mean field not 16-byte aligned");
+    if (for_shape(b, n, [&](Group& g) { g.mean_field = mean_field; }) == 0)
+        return fail(GPE_EINVAL, "no trajectories of shape %d x %d x %d", n[0], n[1], n[2]);
     return GPE_OK;
 }
 

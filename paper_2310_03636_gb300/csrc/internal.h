@@ -33,6 +33,7 @@ struct PassArgs {
     const twel<T>* ph_pre;    // row pass with a leading half kinetic step: its phase table
     const twel<T>* ph;        // phase table exp(-i tau k^2 / 2) / N
     LocalCoef<T> coef;        // couplings for the local step (row pass)
+    const T* vpot;            // row pass: potential [3][sites] shared by the group, or null
     int* status;              // device status word (bounded waits that expire)
 };
 
@@ -49,6 +50,7 @@ struct Res1DArgs {
     int32_t n_knots;
     int64_t nsteps;
     int32_t kind;             // local step: 0 paper scheme, 1 spin rotation
+    const T* vpot;            // potential [3][N] shared by the group, or null
 };
 
 struct NoiseArgs {
@@ -60,6 +62,7 @@ struct NoiseArgs {
     uint32_t key0, key1;
     double sigma;             // sqrt(noise_per_mode / dx^d)
     double mean[6];
+    const double* mean_field; // [3][sites] (re, im) added to the mean, or null
 };
 
 // Trajectories of one shape and spacing, advanced together.
@@ -82,6 +85,8 @@ struct Group {
     void* wn = nullptr;            // cluster 1D: W_N^{n r}, r < cluster, n < M
     CUtensorMap map_y{};           // 2D map {2 nx, ntraj 3 nz ny} of the batch (ndim >= 2)
     CUtensorMap map_z{};           // 3D map {2 nx, ny, nz 3 ntraj} (ndim == 3)
+    const void* vpot = nullptr;    // caller's potential [3][sites] (real, the batch's precision), or null
+    const double* mean_field = nullptr;   // caller's initial mean field [3][sites] complex FP64, or null
 };
 
 // Sets the message gpe_last_error() returns on this thread.

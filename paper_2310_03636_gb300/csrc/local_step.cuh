@@ -1,7 +1,8 @@
 // Per-site nonlinear part of the split step: L(dt) = D(dt/2) O(dt) D(dt/2).
 //
-// D (diagonal step of Sec. 2.2): psi_m <- psi_m exp(-i f_m tau) with the diagonal
-// entries of the operator of Eq. (GPE) (V = 0):
+// D (diagonal step of Sec. 2.2): psi_m <- psi_m exp(-i (V_m + f_m) tau) with the
+// external potential V_m(x) (zero unless the caller sets one) and the diagonal
+// entries of the operator of Eq. (GPE):
 //   f_1  = q + (c0 + c1) rho - 2 c1 |psi_-1|^2
 //   f_0  =     (c0 + c1) rho -   c1 |psi_0|^2        (q - c1 q / c1 = 0)
 //   f_-1 = q + (c0 + c1) rho - 2 c1 |psi_1|^2
@@ -28,13 +29,19 @@ struct LocalCoef {
     int kind;   // 0: the paper's D O D step, 1: exact spin rotation (see local_step_rot)
 };
 
+// External potential at one site: V_1, V_0, V_-1.
+template <typename T>
+struct SitePot {
+    T v1, v0, vm;
+};
+
 template <typename T, typename V>
-__device__ __forceinline__ void diag_phase(V& p1, V& p0, V& pm, T c0, T c1, T q, T tau) {
+__device__ __forceinline__ void diag_phase(V& p1, V& p0, V& pm, T c0, T c1, T q, T tau, SitePot<T> vp) {
     const T n1 = cabs2(p1), n0 = cabs2(p0), nm = cabs2(pm);
     const T g = (c0 + c1) * (n1 + n0 + nm);
-    const T th1 = (q + g - (T)2 * c1 * nm) * tau;
-    const T th0 = (g - c1 * n0) * tau;
-    const T thm = (q + g - (T)2 * c1 * n1) * tau;
+    const T th1 = (vp.v1 + q + g - (T)2 * c1 * nm) * tau;
+    const T th0 = (vp.v0 + g - c1 * n0) * tau;
+    const T thm = (vp.vm + q + g - (T)2 * c1 * n1) * tau;
     T s, c;
     sincos_t(th1, &s, &c);
     p1 = mk(p1.x * c + p1.y * s, p1.y * c - p1.x * s);
@@ -112,14 +119,21 @@ __device__ __forceinline__ float2 rot_minus(float2 p, float ang) {
 //    power series in u = th^2 = lambda^2 (c1 dt)^2 (no square root or division):
 //    sum (-u)^k / (2k+1)! and sum (-u)^k / (2k+2)! to k = 4 for u <= 1/4 (truncation
 //    below 3e-11), the trigonometric form otherwise.
-__device__ __forceinline__ void local_step_fast(float2& p1, float2& p0, float2& pm, const LocalCoef<float>& k) {
+// With HAS_V the potential enters the same angles: V_0 in the common phase, V_+-1 - V_0
+// in the relative ones.
+template <bool HAS_V>
+__device__ __forceinline__ void local_step_fast(float2& p1, float2& p0, float2& pm, const LocalCoef<float>& k,
+                                                SitePot<float> vp) {
     const float h = 0.5f * k.dt;
     const float c0 = k.c0, c1 = k.c1, q = k.q;
+    const float q1 = HAS_V ? q + (vp.v1 - vp.v0) : q;
+    const float qm = HAS_V ? q + (vp.vm - vp.v0) : q;
     // D(dt/2), relative to m = 0
     float n1 = cabs2(p1), n0 = cabs2(p0), nm = cabs2(pm);
-    const float g0 = ((c0 + c1) * (n1 + n0 + nm) - c1 * n0) * h;
-    p1 = rot_minus(p1, (q - 2.0f * c1 * nm + c1 * n0) * h);
-    pm = rot_minus(pm, (q - 2.0f * c1 * n1 + c1 * n0) * h);
+    const float g0 = HAS_V ? ((c0 + c1) * (n1 + n0 + nm) - c1 * n0 + vp.v0) * h
+                           : ((c0 + c1) * (n1 + n0 + nm) - c1 * n0) * h;
+    p1 = rot_minus(p1, (q1 - 2.0f * c1 * nm + c1 * n0) * h);
+    pm = rot_minus(pm, (qm - 2.0f * c1 * n1 + c1 * n0) * h);
     // O(dt)
     const float eps = c1 * k.dt;
     const float2 a = cmulc(pm, p0);
@@ -165,9 +179,10 @@ __device__ __forceinline__ void local_step_fast(float2& p1, float2& p0, float2& 
     n1 = cabs2(p1);
     n0 = cabs2(p0);
     nm = cabs2(pm);
-    const float gg = g0 + ((c0 + c1) * (n1 + n0 + nm) - c1 * n0) * h;
-    p1 = rot_minus(p1, gg + (q - 2.0f * c1 * nm + c1 * n0) * h);
-    pm = rot_minus(pm, gg + (q - 2.0f * c1 * n1 + c1 * n0) * h);
+    const float gg = HAS_V ? g0 + ((c0 + c1) * (n1 + n0 + nm) - c1 * n0 + vp.v0) * h
+                           : g0 + ((c0 + c1) * (n1 + n0 + nm) - c1 * n0) * h;
+    p1 = rot_minus(p1, gg + (q1 - 2.0f * c1 * nm + c1 * n0) * h);
+    pm = rot_minus(pm, gg + (qm - 2.0f * c1 * n1 + c1 * n0) * h);
     p0 = rot_minus(p0, gg);
 }
 
@@ -178,13 +193,24 @@ __device__ __forceinline__ void local_step_fast(float2& p1, float2& p0, float2& 
 //   exp(-i c1 tau F.f) = 1 - i c1 tau s1(th) F.f - (c1 tau)^2 s2(th) (F.f)^2,
 // s1 = sin(th)/th, s2 = (1 - cos th)/th^2 as power series in th^2 (no division).  The
 // q f_z^2 phase is split symmetrically around it: Q(dt/2) R(dt) Q(dt/2).  F_z is kept
-// exactly by every factor.
-template <typename T, typename V>
-__device__ __forceinline__ void local_step_rot(V& p1, V& p0, V& pm, const LocalCoef<T>& k) {
+// exactly by every factor.  A potential V_m is diagonal like q f_z^2 and joins Q.
+template <bool HAS_V, typename T, typename V>
+__device__ __forceinline__ void local_step_rot(V& p1, V& p0, V& pm, const LocalCoef<T>& k, SitePot<T> vp) {
+    const T h = (T)0.5 * k.dt;
     T sq, cq;
-    sincos_t(k.q * (T)0.5 * k.dt, &sq, &cq);
-    p1 = mk(p1.x * cq + p1.y * sq, p1.y * cq - p1.x * sq);
-    pm = mk(pm.x * cq + pm.y * sq, pm.y * cq - pm.x * sq);
+    if constexpr (HAS_V) {
+        T s, c;
+        sincos_t((k.q + vp.v1) * h, &s, &c);
+        p1 = mk(p1.x * c + p1.y * s, p1.y * c - p1.x * s);
+        sincos_t(vp.v0 * h, &s, &c);
+        p0 = mk(p0.x * c + p0.y * s, p0.y * c - p0.x * s);
+        sincos_t((k.q + vp.vm) * h, &s, &c);
+        pm = mk(pm.x * c + pm.y * s, pm.y * c - pm.x * s);
+    } else {
+        sincos_t(k.q * h, &sq, &cq);
+        p1 = mk(p1.x * cq + p1.y * sq, p1.y * cq - p1.x * sq);
+        pm = mk(pm.x * cq + pm.y * sq, pm.y * cq - pm.x * sq);
+    }
     const T n1 = cabs2(p1), n0 = cabs2(p0), nm = cabs2(pm);
     const T rho = n1 + n0 + nm, fz = n1 - nm;
     const V A = cadd(cmulc(p1, p0), cmulc(p0, pm));   // F_+ / sqrt2
@@ -219,32 +245,57 @@ __device__ __forceinline__ void local_step_rot(V& p1, V& p0, V& pm, const LocalC
     const V w1 = cadd(cscale(g1, fz), cmulc(A, g0));
     const V w0 = cadd(cmul(A, g1), cmulc(A, gm));
     const V wm = csub(cmul(A, g0), cscale(gm, fz));
-    T sr, cr;
-    sincos_t(k.c0 * rho * k.dt, &sr, &cr);
     V r1 = mk(p1.x + e1 * g1.y - e2 * w1.x, p1.y - e1 * g1.x - e2 * w1.y);
     V r0 = mk(p0.x + e1 * g0.y - e2 * w0.x, p0.y - e1 * g0.x - e2 * w0.y);
     V rm = mk(pm.x + e1 * gm.y - e2 * wm.x, pm.y - e1 * gm.x - e2 * wm.y);
-    // c0 phase on all three, second half of the q phase on m = +-1
-    const T c1x = cr * cq - sr * sq, s1x = sr * cq + cr * sq;   // exp(-i(c0 rho dt + q dt/2))
-    p1 = mk(r1.x * c1x + r1.y * s1x, r1.y * c1x - r1.x * s1x);
-    p0 = mk(r0.x * cr + r0.y * sr, r0.y * cr - r0.x * sr);
-    pm = mk(rm.x * c1x + rm.y * s1x, rm.y * c1x - rm.x * s1x);
+    const T a0 = k.c0 * rho * k.dt;
+    if constexpr (HAS_V) {
+        // c0 phase and the second half of Q, one angle per component
+        T s, c;
+        sincos_t(a0 + (k.q + vp.v1) * h, &s, &c);
+        p1 = mk(r1.x * c + r1.y * s, r1.y * c - r1.x * s);
+        sincos_t(a0 + vp.v0 * h, &s, &c);
+        p0 = mk(r0.x * c + r0.y * s, r0.y * c - r0.x * s);
+        sincos_t(a0 + (k.q + vp.vm) * h, &s, &c);
+        pm = mk(rm.x * c + rm.y * s, rm.y * c - rm.x * s);
+    } else {
+        T sr, cr;
+        sincos_t(a0, &sr, &cr);
+        // c0 phase on all three, second half of the q phase on m = +-1
+        const T c1x = cr * cq - sr * sq, s1x = sr * cq + cr * sq;   // exp(-i(c0 rho dt + q dt/2))
+        p1 = mk(r1.x * c1x + r1.y * s1x, r1.y * c1x - r1.x * s1x);
+        p0 = mk(r0.x * cr + r0.y * sr, r0.y * cr - r0.x * sr);
+        pm = mk(rm.x * c1x + rm.y * s1x, rm.y * c1x - rm.x * s1x);
+    }
+}
+
+// The local step at one site; HAS_V adds the potential vp (otherwise ignored).
+template <bool HAS_V, typename T, typename V>
+__device__ __forceinline__ void local_step(V& p1, V& p0, V& pm, const LocalCoef<T>& k, SitePot<T> vp) {
+    if (k.kind == 1) {
+        local_step_rot<HAS_V, T>(p1, p0, pm, k, vp);
+        return;
+    }
+    if constexpr (sizeof(T) == 4) {
+        local_step_fast<HAS_V>(p1, p0, pm, k, vp);
+    } else {
+        const T h = (T)0.5 * k.dt;
+        const SitePot<T> v = HAS_V ? vp : SitePot<T>{(T)0, (T)0, (T)0};
+        diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h, v);
+        offdiag_mix<T>(p1, p0, pm, k.c1, k.dt);
+        diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h, v);
+    }
 }
 
 template <typename T, typename V>
 __device__ __forceinline__ void local_step(V& p1, V& p0, V& pm, const LocalCoef<T>& k) {
-    if (k.kind == 1) {
-        local_step_rot<T>(p1, p0, pm, k);
-        return;
-    }
-    if constexpr (sizeof(T) == 4) {
-        local_step_fast(p1, p0, pm, k);
-    } else {
-        const T h = (T)0.5 * k.dt;
-        diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h);
-        offdiag_mix<T>(p1, p0, pm, k.c1, k.dt);
-        diag_phase<T>(p1, p0, pm, k.c0, k.c1, k.q, h);
-    }
+    local_step<false, T>(p1, p0, pm, k, SitePot<T>{(T)0, (T)0, (T)0});
+}
+
+// Potential of site i from a [3][sites] array (comp_stride = sites), or zero.
+template <typename T>
+__device__ __forceinline__ SitePot<T> site_pot(const T* __restrict__ vpot, int64_t comp_stride, int64_t i) {
+    return SitePot<T>{__ldg(vpot + i), __ldg(vpot + comp_stride + i), __ldg(vpot + 2 * comp_stride + i)};
 }
 
 }  // namespace gpe

@@ -1,5 +1,6 @@
-// Truncated-Wigner initial state: mean spinor plus complex Gaussian noise per site and
-// component, Philox4x32-10 integers turned into two FP64 uniforms and a Box-Muller pair.
+// Truncated-Wigner initial state: mean spinor (plus an optional mean field) and complex
+// Gaussian noise per site and component, Philox4x32-10 integers turned into two FP64
+// uniforms and a Box-Muller pair.
 #include "internal.h"
 #include "philox.cuh"
 
@@ -26,8 +27,14 @@ __global__ void __launch_bounds__(256) k_noise(const NoiseArgs a) {
         const double r = sqrt(-log(u1)) * a.sigma;
         double s, c;
         sincospi(2.0 * u2, &s, &c);
+        double mr = a.mean[2 * comp], mi = a.mean[2 * comp + 1];
+        if (a.mean_field) {
+            const double2 f = reinterpret_cast<const double2*>(a.mean_field)[comp * a.sites + site];
+            mr += f.x;
+            mi += f.y;
+        }
         V* out = reinterpret_cast<V*>(a.ptrs[tl]);
-        out[comp * a.sites + site] = mk((T)(a.mean[2 * comp] + r * c), (T)(a.mean[2 * comp + 1] + r * s));
+        out[comp * a.sites + site] = mk((T)(mr + r * c), (T)(mi + r * s));
     }
 }
 

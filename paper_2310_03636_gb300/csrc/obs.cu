@@ -1,7 +1,8 @@
 // Observables pipeline (sample times only; the fields are read, never written):
 //   1. k_obs_prep   real space, per site: copy psi_m and F_perp = sqrt2 (psi_1^* psi_0 +
 //                   psi_0^* psi_-1) into a 4-field workspace; FP64 partial sums of N_m,
-//                   q (n_1 + n_-1), c0 rho^2 / 2, c1 (F_z^2 + |F_perp|^2) / 2 per site block;
+//                   q (n_1 + n_-1), c0 rho^2 / 2, c1 (F_z^2 + |F_perp|^2) / 2 and, with a
+//                   potential, sum_m V_m n_m per site block;
 //   2. forward FFTs of the 4 fields along every axis (same pencil FFT as the propagation);
 //   3. k_obs_ekin   FP64 partial sums of (k^2/2) |psi_m(k)|^2 per mode block;
 //   4. k_obs_bins   per (radial bin, field): sum over trajectories and the bin's modes of
@@ -25,6 +26,7 @@ thread_local std::string g_obs_err;
 
 constexpr int kThreads = 256;
 constexpr int kSitesPerBlock = 4096;
+constexpr int kPartVals = 7;   // real-space partial sums per site block: N_1, N_0, N_-1, E_q, E_c0, E_c1, E_V
 
 gpe_status obs_fail(gpe_status s, const char* what, cudaError_t e) {
     char buf[256];
@@ -65,13 +67,13 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV * 32
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_obs_prep(cplx<T>* const* __restrict__ ptrs, int t0, cplx<T>* __restrict__ W, int64_t sites, double c0,
-           double c1, double q, double* __restrict__ part, int64_t nblk) {
+           double c1, double q, const T* __restrict__ vpot, double* __restrict__ part, int64_t nblk) {
     using V = cplx<T>;
-    __shared__ double sm[6 * 32];
+    __shared__ double sm[kPartVals * 32];
     const int tl = blockIdx.y;
     const V* f = ptrs[t0 + tl];
     V* w = W + (int64_t)tl * 4 * sites;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double acc[kPartVals] = {0, 0, 0, 0, 0, 0, 0};
     const int64_t s0 = (int64_t)blockIdx.x * kSitesPerBlock;
     for (int k = 0; k < kSitesPerBlock / kThreads; ++k) {
         const int64_t i = s0 + k * kThreads + threadIdx.x;
@@ -90,16 +92,17 @@ k_obs_prep(cplx<T>* const* __restrict__ ptrs, int t0, cplx<T>* __restrict__ W, i
         acc[3] += q * (n1 + nm);
         acc[4] += 0.5 * c0 * rho * rho;
         acc[5] += 0.5 * c1 * (fz * fz + fr * fr + fi * fi);
+        if (vpot) acc[6] += (double)vpot[i] * n1 + (double)vpot[sites + i] * n0 + (double)vpot[2 * sites + i] * nm;
         w[i] = p1;
         w[sites + i] = p0;
         w[2 * sites + i] = pm;
         w[3 * sites + i] = mk((T)fr, (T)fi);
     }
-    block_sum<6>(acc, sm);
+    block_sum<kPartVals>(acc, sm);
     if (threadIdx.x == 0) {
-        double* o = part + ((int64_t)tl * nblk + blockIdx.x) * 6;
+        double* o = part + ((int64_t)tl * nblk + blockIdx.x) * kPartVals;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) o[k] = acc[k];
+        for (int k = 0; k < kPartVals; ++k) o[k] = acc[k];
     }
 }
 
@@ -156,25 +159,26 @@ __global__ void __launch_bounds__(kThreads)
 k_obs_final(const double* __restrict__ part, const double* __restrict__ ekin, int64_t nblk, int64_t count,
             const int32_t* __restrict__ ids, int t0, double vol, double inv_sites, double* __restrict__ acc_diag,
             int* status) {
-    __shared__ double sm[7 * 32];
+    __shared__ double sm[8 * 32];
     const int tl = blockIdx.x;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t k = threadIdx.x; k < count; k += kThreads) {
-        const double* p = part + ((int64_t)tl * nblk + k) * 6;
+        const double* p = part + ((int64_t)tl * nblk + k) * kPartVals;
         acc[0] += p[0];
         acc[1] += p[1];
         acc[2] += p[2];
         acc[4] += p[3];
         acc[5] += p[4];
         acc[6] += p[5];
+        acc[7] += p[6];
         acc[3] += ekin[((int64_t)tl * 3 + 0) * nblk + k] + ekin[((int64_t)tl * 3 + 1) * nblk + k] +
                   ekin[((int64_t)tl * 3 + 2) * nblk + k];
     }
-    block_sum<7>(acc, sm);
+    block_sum<8>(acc, sm);
     if (threadIdx.x == 0) {
         double* o = acc_diag + (int64_t)ids[t0 + tl] * 8;
         bool finite = true;
-        for (int k = 0; k < 7; ++k) {
+        for (int k = 0; k < 8; ++k) {
             const double v = (k == 3) ? acc[k] * vol * inv_sites : acc[k] * vol;
             finite = finite && isfinite(v);
             o[k] += v;
@@ -195,7 +199,8 @@ gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q,
     for (int t0 = 0; t0 < g.ntraj; t0 += (int)w.chunk) {
         const int nc = (int)std::min<int64_t>(w.chunk, g.ntraj - t0);
         k_obs_prep<T><<<dim3((unsigned)nblk, nc), kThreads, 0, s>>>(
-            reinterpret_cast<V* const*>(g.dptrs), t0, W, g.sites, c0, c1, q, w.d_part, w.nblk);
+            reinterpret_cast<V* const*>(g.dptrs), t0, W, g.sites, c0, c1, q, reinterpret_cast<const T*>(g.vpot),
+            w.d_part, w.nblk);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs prep", e);
         const twel<T>* twx[3] = {reinterpret_cast<const twel<T>*>(g.tw[0][0]),
@@ -333,7 +338,7 @@ static gpe_status ensure_workspace(ObsWork& w, const std::vector<Group>& groups)
     w.nblk = (max_sites + kSitesPerBlock - 1) / kSitesPerBlock;
     cudaError_t e = cudaMalloc(&w.d_W, (size_t)(w.chunk * per_traj));
     if (e == cudaSuccess) e = cudaMalloc(&w.d_Wptrs, sizeof(void*) * w.chunk);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_part, sizeof(double) * w.chunk * w.nblk * 6);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_part, sizeof(double) * w.chunk * w.nblk * kPartVals);
     if (e == cudaSuccess) e = cudaMalloc(&w.d_ekin, sizeof(double) * w.chunk * w.nblk * 3);
     if (e != cudaSuccess) {
         cudaGetLastError();

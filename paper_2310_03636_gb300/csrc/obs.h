@@ -17,7 +17,7 @@ struct ObsWork {
     int32_t* d_modes = nullptr;      // mode indices sorted by bin, then by index
     void* d_W = nullptr;             // workspace: chunk x 4 fields x sites complex
     void** d_Wptrs = nullptr;        // per chunk slot: its 4-field block
-    double* d_part = nullptr;        // chunk x nblk x 6 real-space partial sums
+    double* d_part = nullptr;        // chunk x nblk x 7 real-space partial sums
     double* d_ekin = nullptr;        // chunk x 3 x nblk kinetic partial sums
     int64_t chunk = 0;               // trajectories per workspace chunk
     int64_t nblk = 0;                // site blocks per trajectory (largest group)

@@ -112,14 +112,29 @@ k_xpass(const PassArgs<T> a) {
         for (int c = 0; c < 3; ++c) kinetic_row<T, N, R>(Dr + c * N, Xr, tws, a.ph_pre, t);
     }
     if (lrow < nrows) {
+        if (a.vpot == nullptr) {
 #pragma unroll 2
-        for (int m = 0; m < R; ++m) {
-            const int i = t + m * TP;
-            V p1 = Dr[i], p0 = Dr[N + i], pm = Dr[2 * N + i];
-            local_step<T>(p1, p0, pm, a.coef);
-            Dr[i] = p1;
-            Dr[N + i] = p0;
-            Dr[2 * N + i] = pm;
+            for (int m = 0; m < R; ++m) {
+                const int i = t + m * TP;
+                V p1 = Dr[i], p0 = Dr[N + i], pm = Dr[2 * N + i];
+                local_step<T>(p1, p0, pm, a.coef);
+                Dr[i] = p1;
+                Dr[N + i] = p0;
+                Dr[2 * N + i] = pm;
+            }
+        } else {
+            const int64_t g = row0 + lrow;
+            const int64_t traj = g / a.rows_per_traj;
+            const T* vrow = a.vpot + (g - traj * a.rows_per_traj) * N;
+#pragma unroll 2
+            for (int m = 0; m < R; ++m) {
+                const int i = t + m * TP;
+                V p1 = Dr[i], p0 = Dr[N + i], pm = Dr[2 * N + i];
+                local_step<true, T>(p1, p0, pm, a.coef, site_pot<T>(vrow, a.comp_stride, i));
+                Dr[i] = p1;
+                Dr[N + i] = p0;
+                Dr[2 * N + i] = pm;
+            }
         }
     }
 #pragma unroll 1
@@ -384,8 +399,14 @@ k_resident1d(const Res1DArgs<T> a) {
     LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
+        if (a.vpot == nullptr) {
 #pragma unroll
-        for (int m = 0; m < R; ++m) local_step<T>(v[0][m], v[1][m], v[2][m], coef);
+            for (int m = 0; m < R; ++m) local_step<T>(v[0][m], v[1][m], v[2][m], coef);
+        } else {
+#pragma unroll
+            for (int m = 0; m < R; ++m)
+                local_step<true, T>(v[0][m], v[1][m], v[2][m], coef, site_pot<T>(a.vpot, N, t + m * TP));
+        }
         fft_pencil<N, R, -1, 3, SY>(v, buf, tws, t);
         const twel<T>* ph = (s == a.nsteps - 1) ? a.ph_half : a.ph_full;
 #pragma unroll

@@ -109,8 +109,14 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
     LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
+        if (a.vpot == nullptr) {
 #pragma unroll
-        for (int m = 0; m < R; ++m) local_step<T>(v[0][m], v[1][m], v[2][m], coef);
+            for (int m = 0; m < R; ++m) local_step<T>(v[0][m], v[1][m], v[2][m], coef);
+        } else {
+#pragma unroll
+            for (int m = 0; m < R; ++m)
+                local_step<true, T>(v[0][m], v[1][m], v[2][m], coef, site_pot<T>(a.vpot, N, rank * M + t + m * TP));
+        }
         kinetic(s == a.nsteps - 1 ? a.ph_half : a.ph_full);
     }
 #pragma unroll
