@@ -366,6 +366,21 @@ def diagnostics(psi, dx, c0, c1, q, d, V=None):
     return torch.cat([N, torch.stack([ekin, eq, ec0, ec1, ev], dim=-1)], dim=-1)
 
 
+def larmor_angle(psi, d):
+    """phi_L = arg(F_x + i F_y), the orientation of the transverse spin (Sec. 1, Fig. 1)."""
+    return torch.angle(transverse_spin(psi, d))
+
+
+def winding_number(psi):
+    """Q_w / (2 pi) of a 1D periodic trajectory (Sec. 1, Fig. 1: Q_w = int dx d_x phi_L):
+    the sum over neighbouring sites of the Larmor-angle increment arg(F(x)^* F(x+1)),
+    each in (-pi, pi], around the ring, divided by 2 pi.  An integer up to rounding
+    whenever F_perp has no zeros.  psi: (..., 3, n)."""
+    F = transverse_spin(psi, 1)
+    inc = torch.angle(F.conj() * torch.roll(F, -1, dims=-1))
+    return inc.sum(dim=-1) / (2.0 * math.pi)
+
+
 def sf_band_loss(psi, dx, d, kmin, kmax):
     """Late-time loss: mean over trajectories of sum_{k: kmin <= |k| <= kmax} S_perp(k),
     summed over grid modes, bounds inclusive.  psi: (ntraj, 3, *shape)."""

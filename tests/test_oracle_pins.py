@@ -405,6 +405,43 @@ def test_rotation_scheme_with_potential_keeps_fz():
     assert float((out - O.propagate_rotation(psi, 0.05, 40, 1.0, -0.5, 0.09, dx, 1)).abs().max()) > 1e-3
 
 
+# ---------------------------------------------------------------- Larmor angle, winding
+
+@pytest.mark.parametrize("j1,j0,jm", [(0, 3, 0), (2, 0, 0), (0, 0, -5), (1, -2, 0), (0, 0, 0)])
+def test_winding_number_of_phase_windings(j1, j0, jm):
+    """psi_1 = a e^{2 pi i j1 x/L}, psi_0 = b e^{2 pi i j0 x/L}, psi_-1 = 0: F_perp is
+    proportional to e^{2 pi i (j0 - j1) x/L}, so Q_w / 2 pi = j0 - j1; with psi_1 = 0 and
+    psi_-1 = c e^{2 pi i jm x/L} instead, F_perp ~ e^{2 pi i (jm - j0) x/L}."""
+    n = 128
+    x = np.arange(n)
+    a, b, c = 0.6, 0.9 * np.exp(0.4j), 0.7
+    if jm == 0:
+        psi = np.stack([a * np.exp(2j * np.pi * j1 * x / n), b * np.exp(2j * np.pi * j0 * x / n), 0 * x])
+        want = j0 - j1
+    else:
+        psi = np.stack([0 * x, b * np.exp(2j * np.pi * j0 * x / n), c * np.exp(2j * np.pi * jm * x / n)])
+        want = jm - j0
+    assert abs(float(O.winding_number(T(psi))) - want) < 1e-12
+    phi = O.larmor_angle(T(psi), 1).numpy()
+    np.testing.assert_allclose(np.exp(1j * phi), np.exp(1j * (np.angle(np.conj(psi[0]) * psi[1] + np.conj(psi[1]) * psi[2]))),
+                               atol=1e-12)
+
+
+def test_winding_number_against_unwrap_and_symmetries():
+    """Random spinors: an integer equal to the net turn of numpy's unwrapped Larmor angle,
+    unchanged by a global phase and by a spin rotation about z (F_perp -> e^{-i a} F_perp)."""
+    n = 256
+    for seed in range(6):
+        psi = W.random_field((n,), 1, seed=100 + seed, scale=0.8, mean=(0.3, 0.2, 0.1))[0]
+        w = float(O.winding_number(T(psi)))
+        assert abs(w - round(w)) < 1e-10
+        F = math.sqrt(2.0) * (np.conj(psi[0]) * psi[1] + np.conj(psi[1]) * psi[2])
+        ang = np.unwrap(np.angle(np.append(F, F[0])))
+        assert abs((ang[-1] - ang[0]) / (2 * np.pi) - w) < 1e-10
+        rot = psi * np.exp(-1j * 0.7 * np.array([1.0, 0.0, -1.0]))[:, None] * np.exp(0.3j)
+        assert abs(float(O.winding_number(T(rot))) - w) < 1e-10
+
+
 # ---------------------------------------------------------------- observables
 
 def _brute_dft(f, dx):
