@@ -102,7 +102,8 @@ gpe_status gpe_step_batch(gpe_batch* batch, int64_t nsteps, void* stream);
 
 /* Observable flags. */
 #define GPE_OBS_SPECTRA 1u   /* n_1, n_0, n_-1 and S_perp, radially binned, summed over trajectories */
-#define GPE_OBS_DIAG    2u   /* per-trajectory N_1, N_0, N_-1, E_kin, E_q, E_c0, E_c1              */
+#define GPE_OBS_DIAG    2u   /* per-trajectory N_1, N_0, N_-1, E_kin, E_q, E_c0, E_c1, E_V         */
+#define GPE_OBS_WINDING 4u   /* per-trajectory winding number of the Larmor angle (1D batches)     */
 
 /* Accumulates observables of the current fields into acc (caller-owned device FP64):
  * acc += contributions, at offset sample_slot * slot_doubles (see gpe_obs_layout).
@@ -114,17 +115,22 @@ gpe_status gpe_step_batch(gpe_batch* batch, int64_t nsteps, void* stream);
  * with bin b = round(|k| / (2 pi / L)); then [ntraj][8] diagnostics (N_1, N_0, N_-1,
  * E_kin, E_q, E_c0, E_c1, E_V), E = dx^d sum_x [psi^*(-Laplacian/2)psi + q (n_1 + n_-1)
  * + c0 rho^2 / 2 + c1 (F_z^2 + |F_perp|^2) / 2 + sum_m V_m n_m] at the current q
- * (E_V = 0 without a potential).  Sums are
+ * (E_V = 0 without a potential); then [ntraj] winding numbers Q_w / (2 pi) of the Larmor
+ * angle phi_L = arg(F_perp) (Sec. 1: Q_w = int dx d_x phi_L), each the sum over x of
+ * arg(F_perp(x)^* F_perp(x+1)) in (-pi, pi] around the periodic grid, an integer up to
+ * rounding (1D trajectories only).  Sums are
  * deterministic (fixed reduction order).  The fields are not modified.  The first call
  * on a batch allocates the handle's spectra workspace (four fields per trajectory, in
  * chunks of at most 1 GiB); make it before capturing a stream.
  * Errors: GPE_EINVAL (NULL acc, sample_slot < 0, unknown flags), GPE_EUNSUPPORTED
- * (spectra requested for a batch with more than one shape or unequal sides). */
+ * (spectra requested for a batch with more than one shape or unequal sides; spectra or
+ * diagnostics for x extents above 4096; the winding number for a batch with 2D or 3D
+ * trajectories).  The winding number alone allocates no workspace. */
 gpe_status observables_accumulate(gpe_batch* batch, double* acc, uint32_t flags,
                                   int32_t sample_slot, void* stream);
 
 /* Accumulator geometry: number of radial bins (0 if spectra are unavailable) and the
- * number of doubles per sample slot (4 * nbins + 8 * ntraj). */
+ * number of doubles per sample slot (4 * nbins + 9 * ntraj). */
 gpe_status gpe_obs_layout(const gpe_batch* batch, int32_t* nbins, int64_t* slot_doubles);
 
 /* Number of grid modes in each radial bin (host array of nbins int64). */

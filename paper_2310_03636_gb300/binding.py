@@ -14,7 +14,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgpe.so"
 
 GPE_OK, GPE_EINVAL, GPE_ENOMEM, GPE_ECUDA, GPE_ETIMEOUT, GPE_ENONFINITE, GPE_EUNSUPPORTED = range(7)
 GPE_C64, GPE_C128 = 0, 1
-GPE_OBS_SPECTRA, GPE_OBS_DIAG = 1, 2
+GPE_OBS_SPECTRA, GPE_OBS_DIAG, GPE_OBS_WINDING = 1, 2, 4
 GPE_INTEGRATOR_PAPER, GPE_INTEGRATOR_ROTATION = 0, 1
 STATUS_NAMES = {0: "GPE_OK", 1: "GPE_EINVAL", 2: "GPE_ENOMEM", 3: "GPE_ECUDA", 4: "GPE_ETIMEOUT",
                 5: "GPE_ENONFINITE", 6: "GPE_EUNSUPPORTED"}
@@ -343,3 +343,10 @@ def unpack_slot(acc_slot, nbins, ntraj):
     spec = a[:4 * nbins].reshape(4, nbins) if nbins > 0 else np.zeros((4, 0))
     diag = a[4 * max(nbins, 0):4 * max(nbins, 0) + 8 * ntraj].reshape(ntraj, 8)
     return spec, diag
+
+
+def unpack_winding(acc_slot, nbins, ntraj):
+    """Per-trajectory winding numbers Q_w / 2 pi of one accumulator slot."""
+    a = acc_slot.detach().cpu().numpy() if torch.is_tensor(acc_slot) else np.asarray(acc_slot)
+    o = 4 * max(nbins, 0) + 8 * ntraj
+    return a[o:o + ntraj].copy()

@@ -643,7 +643,7 @@ gpe_status observables_accumulate(gpe_batch* b, double* acc, uint32_t flags, int
     if (!b) return fail(GPE_EINVAL, "batch is NULL");
     if (!acc) return fail(GPE_EINVAL, "acc is NULL");
     if (slot < 0) return fail(GPE_EINVAL, "sample_slot < 0");
-    if (flags & ~(GPE_OBS_SPECTRA | GPE_OBS_DIAG)) return fail(GPE_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~(GPE_OBS_SPECTRA | GPE_OBS_DIAG | GPE_OBS_WINDING)) return fail(GPE_EINVAL, "unknown flags 0x%x", flags);
     if ((flags & GPE_OBS_SPECTRA) && b->obs.nbins <= 0)
         return fail(GPE_EUNSUPPORTED, "spectra need one shape with equal side lengths");
     const double q = q_at_host(b, (double)b->step * b->p.dt);
@@ -657,7 +657,7 @@ gpe_status observables_accumulate(gpe_batch* b, double* acc, uint32_t flags, int
 gpe_status gpe_obs_layout(const gpe_batch* b, int32_t* nbins, int64_t* slot_doubles) {
     if (!b || !nbins || !slot_doubles) return fail(GPE_EINVAL, "NULL argument");
     *nbins = b->obs.nbins;
-    *slot_doubles = (int64_t)4 * (b->obs.nbins > 0 ? b->obs.nbins : 0) + 8 * (int64_t)b->trajs.size();
+    *slot_doubles = (int64_t)4 * (b->obs.nbins > 0 ? b->obs.nbins : 0) + 9 * (int64_t)b->trajs.size();
     return GPE_OK;
 }
 

@@ -9,6 +9,8 @@
 //                   |W|^2 dx^d / N (- 1/2 for the occupations), FP64, into the caller's
 //                   accumulator;
 //   5. k_obs_final  per trajectory: the partial sums in fixed order into the accumulator.
+// Separately, k_obs_winding (1D only, reads the fields directly): the winding number of
+// the Larmor angle per trajectory.
 // Every reduction has a fixed order (per-thread strided sums, shuffle trees, warp sums
 // combined in index order), so results are bitwise reproducible.
 #include <cmath>
@@ -187,12 +189,49 @@ k_obs_final(const double* __restrict__ part, const double* __restrict__ ekin, in
     }
 }
 
+// Winding number of the Larmor angle phi_L = arg(F_perp) around a periodic 1D trajectory
+// (Sec. 1: Q_w = int dx d_x phi_L), in units of 2 pi: the sum over x of the increments
+// arg(F(x)^* F(x+1)) in (-pi, pi], FP64, fixed summation order.  One block per trajectory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_obs_winding(cplx<T>* const* __restrict__ ptrs, const int32_t* __restrict__ ids, int64_t n,
+              double* __restrict__ acc_wind, int* status) {
+    using V = cplx<T>;
+    __shared__ double sm[32];
+    const V* f = ptrs[blockIdx.x];
+    auto fperp = [&](int64_t i) {   // conj(p1) p0 + conj(p0) pm (the factor sqrt2 drops out)
+        const V p1 = f[i], p0 = f[n + i], pm = f[2 * n + i];
+        const double r = ((double)p1.x * p0.x + (double)p1.y * p0.y) + ((double)p0.x * pm.x + (double)p0.y * pm.y);
+        const double im = ((double)p1.x * p0.y - (double)p1.y * p0.x) + ((double)p0.x * pm.y - (double)p0.y * pm.x);
+        return make_double2(r, im);
+    };
+    double acc[1] = {0.0};
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) {
+        const double2 a = fperp(i), b = fperp(i + 1 == n ? 0 : i + 1);
+        acc[0] += atan2(a.x * b.y - a.y * b.x, a.x * b.x + a.y * b.y);
+    }
+    block_sum<1>(acc, sm);
+    if (threadIdx.x == 0) {
+        const double v = acc[0] / 6.283185307179586476925286766559;
+        if (!isfinite(v)) atomicCAS(status, 0, (int)GPE_ENONFINITE);
+        acc_wind[ids[blockIdx.x]] += v;
+    }
+}
+
 template <typename T>
 gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q, double* acc, uint32_t flags,
                      int slot, int* d_status, cudaStream_t s) {
     using V = cplx<T>;
-    const int64_t slot_doubles = 4 * (int64_t)(w.nbins > 0 ? w.nbins : 0) + 8 * w.ntraj_total;
+    const int64_t nb4 = 4 * (int64_t)(w.nbins > 0 ? w.nbins : 0);
+    const int64_t slot_doubles = nb4 + 9 * w.ntraj_total;
     double* acc_slot = acc + (int64_t)slot * slot_doubles;
+    if (flags & GPE_OBS_WINDING) {
+        k_obs_winding<T><<<g.ntraj, kThreads, 0, s>>>(reinterpret_cast<V* const*>(g.dptrs), g.d_ids, g.sites,
+                                                    acc_slot + nb4 + 8 * w.ntraj_total, d_status);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs winding", e);
+    }
+    if (!(flags & (GPE_OBS_SPECTRA | GPE_OBS_DIAG))) return GPE_OK;
     const int64_t nblk = (g.sites + kSitesPerBlock - 1) / kSitesPerBlock;
     const double vol = std::pow(g.dx, g.ndim);
     V* W = reinterpret_cast<V*>(w.d_W);
@@ -268,8 +307,9 @@ int64_t obs_launches(const ObsWork& w, const std::vector<Group>& groups, uint32_
         for (const Group& h : groups) max_traj = std::max<int64_t>(max_traj, h.ntraj);
         const int64_t c = chunk > 0 ? chunk : max_traj;  // before the first call: estimate
         const int64_t nchunks = (g.ntraj + c - 1) / c;
-        const int64_t per = 1 + g.ndim + ((flags & GPE_OBS_DIAG) ? 2 : 0) + ((flags & GPE_OBS_SPECTRA) ? 1 : 0);
-        n += nchunks * per;
+        const bool fields = flags & (GPE_OBS_SPECTRA | GPE_OBS_DIAG);
+        const int64_t per = (fields ? 1 + g.ndim : 0) + ((flags & GPE_OBS_DIAG) ? 2 : 0) + ((flags & GPE_OBS_SPECTRA) ? 1 : 0);
+        n += nchunks * per + ((flags & GPE_OBS_WINDING) ? 1 : 0);
     }
     return n;
 }
@@ -354,13 +394,22 @@ static gpe_status ensure_workspace(ObsWork& w, const std::vector<Group>& groups)
 
 gpe_status obs_accumulate(ObsWork& w, const std::vector<Group>& groups, bool f64, double c0, double c1, double q,
                           double* acc, uint32_t flags, int slot, int* d_status, cudaStream_t s) {
-    for (const Group& g : groups)
-        if (g.n[0] > 4096) {
-            g_obs_err = "observables support x extents up to 4096";
+    const bool fields = flags & (GPE_OBS_SPECTRA | GPE_OBS_DIAG);
+    for (const Group& g : groups) {
+        if (fields && g.n[0] > 4096) {
+            g_obs_err = "spectra and diagnostics support x extents up to 4096";
             return GPE_EUNSUPPORTED;
         }
-    gpe_status st = ensure_workspace(w, groups);
-    if (st != GPE_OK) return st;
+        if ((flags & GPE_OBS_WINDING) && g.ndim != 1) {
+            g_obs_err = "the winding number is defined for 1D trajectories only";
+            return GPE_EUNSUPPORTED;
+        }
+    }
+    if (fields) {
+        gpe_status st = ensure_workspace(w, groups);
+        if (st != GPE_OK) return st;
+    }
+    gpe_status st = GPE_OK;
     for (const Group& g : groups) {
         st = f64 ? run_group<double>(w, g, c0, c1, q, acc, flags, slot, d_status, s)
                  : run_group<float>(w, g, c0, c1, q, acc, flags, slot, d_status, s);
