@@ -85,11 +85,13 @@ __device__ __forceinline__ void offdiag_mix(V& p1, V& p0, V& pm, T c1, T dt) {
     pm = mk(pm.x + e1 * um.y - e2 * wm.x, pm.y - e1 * um.x - e2 * wm.y);
 }
 
-// sin and cos of x: Taylor polynomials for |x| <= 1/2 (truncation below 2e-11),
-// otherwise the range-reduced routine.
-__device__ __forceinline__ void sincos_small(float x, float* s, float* c) {
+// sin x and cos x - 1: Taylor polynomials for |x| <= 1/2 (truncation below 2e-11), so
+// cos x - 1 keeps its relative accuracy for small x; otherwise the range-reduced routine.
+__device__ __forceinline__ void sincosm1(float x, float* s, float* cm1) {
     if (fabsf(x) > 0.5f) {
-        sincos_t(x, s, c);
+        float c;
+        sincos_t(x, s, &c);
+        *cm1 = c - 1.0f;
         return;
     }
     const float x2 = x * x;
@@ -101,13 +103,25 @@ __device__ __forceinline__ void sincos_small(float x, float* s, float* c) {
     pc = fmaf(pc, x2, -1.38888888888888889e-3f);
     pc = fmaf(pc, x2, 4.16666666666666667e-2f);
     pc = fmaf(pc, x2, -0.5f);
-    *c = fmaf(pc, x2, 1.0f);
+    *cm1 = pc * x2;
+}
+__device__ __forceinline__ void sincosm1(double x, double* s, double* cm1) {
+    double c;
+    sincos(x, s, &c);
+    *cm1 = c - 1.0;
 }
 
-__device__ __forceinline__ float2 rot_minus(float2 p, float ang) {
-    float s, c;
-    sincos_small(ang, &s, &c);
-    return make_float2(p.x * c + p.y * s, p.y * c - p.x * s);
+// p e^{-i ang}, written p + [p (cos ang - 1) - i p sin ang] so that the rotation changes
+// |p| only through the rounding of that final sum (unbiased).  The direct form
+// p cos + ... is biased in FP32: near 1, fl(cos) carries a relative error of up to
+// 2^-25 that is the same for every site and step when the angle barely varies (a
+// constant q dt/2, or angles below 2.4e-4, where fl(cos) = 1 while sin != 0), and
+// |p|^2 then drifts by up to ~1e-7 per step.
+template <typename T, typename V>
+__device__ __forceinline__ V rot_minus(V p, T ang) {
+    T s, cm1;
+    sincosm1(ang, &s, &cm1);
+    return mk(p.x + (p.x * cm1 + p.y * s), p.y + (p.y * cm1 - p.x * s));
 }
 
 // FP32 local step, same operator as D(dt/2) O(dt) D(dt/2) but arranged for fewer
@@ -197,20 +211,10 @@ __device__ __forceinline__ void local_step_fast(float2& p1, float2& p0, float2& 
 template <bool HAS_V, typename T, typename V>
 __device__ __forceinline__ void local_step_rot(V& p1, V& p0, V& pm, const LocalCoef<T>& k, SitePot<T> vp) {
     const T h = (T)0.5 * k.dt;
-    T sq, cq;
-    if constexpr (HAS_V) {
-        T s, c;
-        sincos_t((k.q + vp.v1) * h, &s, &c);
-        p1 = mk(p1.x * c + p1.y * s, p1.y * c - p1.x * s);
-        sincos_t(vp.v0 * h, &s, &c);
-        p0 = mk(p0.x * c + p0.y * s, p0.y * c - p0.x * s);
-        sincos_t((k.q + vp.vm) * h, &s, &c);
-        pm = mk(pm.x * c + pm.y * s, pm.y * c - pm.x * s);
-    } else {
-        sincos_t(k.q * h, &sq, &cq);
-        p1 = mk(p1.x * cq + p1.y * sq, p1.y * cq - p1.x * sq);
-        pm = mk(pm.x * cq + pm.y * sq, pm.y * cq - pm.x * sq);
-    }
+    const T v1 = HAS_V ? vp.v1 : (T)0, v0 = HAS_V ? vp.v0 : (T)0, vm = HAS_V ? vp.vm : (T)0;
+    p1 = rot_minus(p1, (k.q + v1) * h);
+    pm = rot_minus(pm, (k.q + vm) * h);
+    if (HAS_V) p0 = rot_minus(p0, v0 * h);
     const T n1 = cabs2(p1), n0 = cabs2(p0), nm = cabs2(pm);
     const T rho = n1 + n0 + nm, fz = n1 - nm;
     const V A = cadd(cmulc(p1, p0), cmulc(p0, pm));   // F_+ / sqrt2
@@ -248,25 +252,11 @@ __device__ __forceinline__ void local_step_rot(V& p1, V& p0, V& pm, const LocalC
     V r1 = mk(p1.x + e1 * g1.y - e2 * w1.x, p1.y - e1 * g1.x - e2 * w1.y);
     V r0 = mk(p0.x + e1 * g0.y - e2 * w0.x, p0.y - e1 * g0.x - e2 * w0.y);
     V rm = mk(pm.x + e1 * gm.y - e2 * wm.x, pm.y - e1 * gm.x - e2 * wm.y);
+    // c0 phase on all three and the second half of Q, one angle per component
     const T a0 = k.c0 * rho * k.dt;
-    if constexpr (HAS_V) {
-        // c0 phase and the second half of Q, one angle per component
-        T s, c;
-        sincos_t(a0 + (k.q + vp.v1) * h, &s, &c);
-        p1 = mk(r1.x * c + r1.y * s, r1.y * c - r1.x * s);
-        sincos_t(a0 + vp.v0 * h, &s, &c);
-        p0 = mk(r0.x * c + r0.y * s, r0.y * c - r0.x * s);
-        sincos_t(a0 + (k.q + vp.vm) * h, &s, &c);
-        pm = mk(rm.x * c + rm.y * s, rm.y * c - rm.x * s);
-    } else {
-        T sr, cr;
-        sincos_t(a0, &sr, &cr);
-        // c0 phase on all three, second half of the q phase on m = +-1
-        const T c1x = cr * cq - sr * sq, s1x = sr * cq + cr * sq;   // exp(-i(c0 rho dt + q dt/2))
-        p1 = mk(r1.x * c1x + r1.y * s1x, r1.y * c1x - r1.x * s1x);
-        p0 = mk(r0.x * cr + r0.y * sr, r0.y * cr - r0.x * sr);
-        pm = mk(rm.x * c1x + rm.y * s1x, rm.y * c1x - rm.x * s1x);
-    }
+    p1 = rot_minus(r1, a0 + (k.q + v1) * h);
+    p0 = rot_minus(r0, a0 + v0 * h);
+    pm = rot_minus(rm, a0 + (k.q + vm) * h);
 }
 
 // The local step at one site; HAS_V adds the potential vp (otherwise ignored).

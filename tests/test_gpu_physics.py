@@ -71,7 +71,7 @@ def test_coarsening_driver_small(B):
     res, arr = coarsening1d.run(n=1024, ntraj=8, dt=0.04, t_end=400.0, nsamples=6, t_first=40.0, t_fit=100.0,
                                 kmax_ir=0.3)
     assert res["steps"] == 10000
-    assert res["norm_drift"] < 1e-4
+    assert res["norm_drift"] < 2e-5
     assert res["winding_integer_dev"] < 1e-6
     assert arr["S_perp"].shape == (len(arr["times"]), 513)
     # S_perp grows out of the initial noise level in the unstable band
