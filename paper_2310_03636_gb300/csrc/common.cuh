@@ -54,11 +54,15 @@ __device__ __forceinline__ double2 twmul(double2 w, double2 f) {
     const double fy = DIR < 0 ? f.y : -f.y;
     return mk(w.x * f.x - w.y * fy, w.x * fy + w.y * f.x);
 }
-// x * c for a compile-time constant c given in double: FP32 uses c_hi + c_lo.
+// x * c for a compile-time constant c given in double: FP32 uses c_hi + c_lo, with the
+// small product x c_lo added inside the fma that forms the exact x c_hi, so the result is
+// x c rounded once.  (Rounding x c_hi first and adding x c_lo afterwards would lose the
+// correction, which is below half an ulp: every product would then carry the constant's
+// own rounding error, the same sign in every transform, and the norm would drift.)
 __device__ __forceinline__ float mulc(float x, double c) {
     const float hi = (float)c;
     const float lo = (float)(c - (double)hi);
-    return fmaf(x, lo, x * hi);
+    return fmaf(x, hi, x * lo);
 }
 __device__ __forceinline__ double mulc(double x, double c) { return x * c; }
 
