@@ -1,7 +1,10 @@
 """Universal coarsening of the 1D spin-1 gas after a quench into the easy-plane phase
 (Sec. 1, Figs. 1-2; Sec. 2.2 for the method): many truncated-Wigner trajectories start
 from the polar state psi_0 = sqrt(n) with half a particle of noise per mode and evolve
-with 0 < q < 2 n |c1| (c1 < 0).  At logarithmically spaced times the library accumulates
+with 0 < q < 2 n |c1| (c1 < 0).  The couplings are given as c0 n and c1 n, so that the
+density n (atoms per lattice cell) sets only the relative size of the initial quantum
+noise; it must be large (the default is 1000) for the noise to seed, rather than swamp,
+the spin instability.  At logarithmically spaced times the library accumulates
 the transverse spin structure factor S_perp(k, t), the diagnostics and the winding number
 of the Larmor angle per trajectory; the host then fits the IR scaling exponents of
 Eq. (StructureFactor) (scaling.py).  Every propagation step and every observable runs in
@@ -27,8 +30,9 @@ def sample_steps(nsteps, nsamples, first):
     return [int(x) for x in s]
 
 
-def run(n=4096, ntraj=304, dt=0.04, t_end=4.0e4, nsamples=20, t_first=200.0, c0=1.0, c1=-0.1, q=0.09,
-        density=1.0, seed=20231005, dtype="c64", chunk=2500, kmax_ir=0.15, t_fit=2000.0):
+def run(n=4096, ntraj=304, dt=0.04, t_end=4.0e4, nsamples=20, t_first=200.0, c0n=1.0, c1n=-0.1, q=0.09,
+        density=1000.0, seed=20231005, dtype="c64", chunk=2500, kmax_ir=0.15, t_fit=2000.0):
+    c0, c1 = c0n / density, c1n / density
     nsteps = int(round(t_end / dt))
     steps = sample_steps(nsteps, nsamples, int(round(t_first / dt)))
     b = B.GPEBatch((n,), ntraj, dtype, c0, c1, q, dt)
@@ -67,7 +71,7 @@ def run(n=4096, ntraj=304, dt=0.04, t_end=4.0e4, nsamples=20, t_first=200.0, c0=
     b.close()
     kbin = 2 * np.pi * np.arange(nb) / n
     late = times >= t_fit
-    res = {"n": n, "ntraj": ntraj, "dt": dt, "t_end": nsteps * dt, "c0": c0, "c1": c1, "q": q, "density": density,
+    res = {"n": n, "ntraj": ntraj, "dt": dt, "t_end": nsteps * dt, "c0n": c0n, "c1n": c1n, "q": q, "density": density,
            "dtype": dtype, "steps": nsteps, "wall_s": wall,
            "site_updates_per_s": n * 3.0 * nsteps * ntraj / wall,
            "norm_drift": float(np.abs(N[-1] / N[0] - 1.0).max()),
@@ -93,16 +97,17 @@ def main():
     p.add_argument("--samples", type=int, default=20)
     p.add_argument("--t-first", type=float, default=200.0)
     p.add_argument("--q", type=float, default=0.09)
-    p.add_argument("--c0", type=float, default=1.0)
-    p.add_argument("--c1", type=float, default=-0.1)
+    p.add_argument("--c0n", type=float, default=1.0, help="c0 times the density")
+    p.add_argument("--c1n", type=float, default=-0.1, help="c1 times the density")
+    p.add_argument("--density", type=float, default=1000.0, help="atoms per lattice cell")
     p.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     p.add_argument("--kmax-ir", type=float, default=0.15)
     p.add_argument("--t-fit", type=float, default=2000.0)
     p.add_argument("--seed", type=int, default=20231005)
     p.add_argument("--out", default=None, help="write the spectra and windings to this .npz")
     a = p.parse_args()
-    res, arrays = run(a.n, a.ntraj, a.dt, a.t_end, a.samples, a.t_first, a.c0, a.c1, a.q, seed=a.seed,
-                      dtype=a.dtype, kmax_ir=a.kmax_ir, t_fit=a.t_fit)
+    res, arrays = run(a.n, a.ntraj, a.dt, a.t_end, a.samples, a.t_first, a.c0n, a.c1n, a.q, a.density,
+                      seed=a.seed, dtype=a.dtype, kmax_ir=a.kmax_ir, t_fit=a.t_fit)
     if a.out:
         np.savez_compressed(a.out, **arrays)
     print(json.dumps(res))

@@ -74,7 +74,8 @@ def test_coarsening_driver_small(B):
     assert res["norm_drift"] < 2e-5
     assert res["winding_integer_dev"] < 1e-6
     assert arr["S_perp"].shape == (len(arr["times"]), 513)
-    # S_perp grows out of the initial noise level in the unstable band
+    # the spin instability of the polar state (unstable band k^2/2 < 2 n |c1| - q) lifts
+    # S_perp far above its initial noise level there
     kq = (arr["k"] > 0.05) & (arr["k"] < 0.4)
     assert arr["S_perp"][-1][kq].mean() > 10 * arr["S_perp"][0][kq].mean()
     for key in ("beta_moment", "beta_collapse"):
