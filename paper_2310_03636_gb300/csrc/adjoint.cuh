@@ -229,9 +229,9 @@ __device__ __forceinline__ void offdiag_fwd(V (&r)[3], T c1, T dt) {
     const V w1 = cmul(A, v0);
     const V w0 = cadd(cmulc(A, v1), cmul(B, vm));
     const V wm = cmulc(B, v0);
-    r[0] = mk(r[0].x + e1 * v1.y - e2 * w1.x, r[0].y - e1 * v1.x - e2 * w1.y);
-    r[1] = mk(r[1].x + e1 * v0.y - e2 * w0.x, r[1].y - e1 * v0.x - e2 * w0.y);
-    r[2] = mk(r[2].x + e1 * vm.y - e2 * wm.x, r[2].y - e1 * vm.x - e2 * wm.y);
+    r[0] = mk(r[0].x + (e1 * v1.y - e2 * w1.x), r[0].y - (e1 * v1.x + e2 * w1.y));
+    r[1] = mk(r[1].x + (e1 * v0.y - e2 * w0.x), r[1].y - (e1 * v0.x + e2 * w0.y));
+    r[2] = mk(r[2].x + (e1 * vm.y - e2 * wm.x), r[2].y - (e1 * vm.x + e2 * wm.y));
 }
 
 // Pullback of the whole local step at input p (= the state after the leading half

@@ -79,10 +79,10 @@ __device__ __forceinline__ void offdiag_mix(V& p1, V& p0, V& pm, T c1, T dt) {
     const V w1 = cmul(A, u0);
     const V w0 = cadd(cmulc(A, u1), cmul(B, um));
     const V wm = cmulc(B, u0);
-    // psi - i e1 u - e2 w
-    p1 = mk(p1.x + e1 * u1.y - e2 * w1.x, p1.y - e1 * u1.x - e2 * w1.y);
-    p0 = mk(p0.x + e1 * u0.y - e2 * w0.x, p0.y - e1 * u0.x - e2 * w0.y);
-    pm = mk(pm.x + e1 * um.y - e2 * wm.x, pm.y - e1 * um.x - e2 * wm.y);
+    // psi + (-i e1 u - e2 w): the change is formed first and added once (see local_step_fast)
+    p1 = mk(p1.x + (e1 * u1.y - e2 * w1.x), p1.y - (e1 * u1.x + e2 * w1.y));
+    p0 = mk(p0.x + (e1 * u0.y - e2 * w0.x), p0.y - (e1 * u0.x + e2 * w0.y));
+    pm = mk(pm.x + (e1 * um.y - e2 * wm.x), pm.y - (e1 * um.x + e2 * wm.y));
 }
 
 // sin x and cos x - 1: Taylor polynomials for |x| <= 1/2 (truncation below 2e-11), so
@@ -186,9 +186,13 @@ __device__ __forceinline__ void local_step_fast(float2& p1, float2& p0, float2& 
     const float2 w1 = cmul(A, u0);
     const float2 w0 = cadd(cmulc(A, u1), cmul(B, um));
     const float2 wm = cmulc(B, u0);
-    p1 = make_float2(p1.x + e1 * u1.y - e2 * w1.x, p1.y - e1 * u1.x - e2 * w1.y);
-    p0 = make_float2(p0.x + e1 * u0.y - e2 * w0.x, p0.y - e1 * u0.x - e2 * w0.y);
-    pm = make_float2(pm.x + e1 * um.y - e2 * wm.x, pm.y - e1 * um.x - e2 * wm.y);
+    // psi + (-i e1 u - e2 w), the change formed first and added with one rounding.  Adding
+    // -i e1 u and -e2 w to psi one after the other loses the second-order term wherever it
+    // is below half an ulp of psi (psi_0 while the spin modes are still small): the
+    // first-order transfer into psi_+-1 then goes uncompensated and |psi|^2 grows.
+    p1 = make_float2(p1.x + (e1 * u1.y - e2 * w1.x), p1.y - (e1 * u1.x + e2 * w1.y));
+    p0 = make_float2(p0.x + (e1 * u0.y - e2 * w0.x), p0.y - (e1 * u0.x + e2 * w0.y));
+    pm = make_float2(pm.x + (e1 * um.y - e2 * wm.x), pm.y - (e1 * um.x + e2 * wm.y));
     // D(dt/2) with the deferred m = 0 phases of both halves
     n1 = cabs2(p1);
     n0 = cabs2(p0);
@@ -249,9 +253,9 @@ __device__ __forceinline__ void local_step_rot(V& p1, V& p0, V& pm, const LocalC
     const V w1 = cadd(cscale(g1, fz), cmulc(A, g0));
     const V w0 = cadd(cmul(A, g1), cmulc(A, gm));
     const V wm = csub(cmul(A, g0), cscale(gm, fz));
-    V r1 = mk(p1.x + e1 * g1.y - e2 * w1.x, p1.y - e1 * g1.x - e2 * w1.y);
-    V r0 = mk(p0.x + e1 * g0.y - e2 * w0.x, p0.y - e1 * g0.x - e2 * w0.y);
-    V rm = mk(pm.x + e1 * gm.y - e2 * wm.x, pm.y - e1 * gm.x - e2 * wm.y);
+    V r1 = mk(p1.x + (e1 * g1.y - e2 * w1.x), p1.y - (e1 * g1.x + e2 * w1.y));
+    V r0 = mk(p0.x + (e1 * g0.y - e2 * w0.x), p0.y - (e1 * g0.x + e2 * w0.y));
+    V rm = mk(pm.x + (e1 * gm.y - e2 * wm.x), pm.y - (e1 * gm.x + e2 * wm.y));
     // c0 phase on all three and the second half of Q, one angle per component
     const T a0 = k.c0 * rho * k.dt;
     p1 = rot_minus(r1, a0 + (k.q + v1) * h);
