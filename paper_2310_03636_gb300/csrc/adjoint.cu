@@ -81,7 +81,7 @@ k_xkin(const AdjArgs<T> a, cplx<T>* __restrict__ field) {
     for (int m = 0; m < R; ++m) {
         const twel<T> f = a.ph[t + m * TP];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) v[c][m] = twmul<CONJ ? +1 : -1>(v[c][m], f);
+        for (int c = 0; c < 3; ++c) v[c][m] = phmul<CONJ ? +1 : -1>(v[c][m], f);
     }
     fft_pencil<N, R, +1, 3, Sync::Block>(v, buf, tws, t);
     if (valid) {
@@ -148,7 +148,7 @@ k_xadj(const AdjArgs<T> a, cplx<T>* __restrict__ lam, const cplx<T>* __restrict_
         for (int m = 0; m < R; ++m) {
             const twel<T> f = a.ph[t + m * TP];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][m] = twmul<+1>(v[c][m], f);
+            for (int c = 0; c < 3; ++c) v[c][m] = phmul<+1>(v[c][m], f);
         }
         fft_pencil<N, R, +1, 3, Sync::Block>(v, buf, tws, t);
     }

@@ -54,6 +54,24 @@ __device__ __forceinline__ double2 twmul(double2 w, double2 f) {
     const double fy = DIR < 0 ? f.y : -f.y;
     return mk(w.x * f.x - w.y * fy, w.x * fy + w.y * f.x);
 }
+
+// The same product for a kinetic phase-table entry, with the cosine products w f.x as the
+// outer fma of both components.  The kinetic phases of the IR modes are small angles: there
+// f.x_hi is 1 or a few ulps below it, so w.y f.x_hi is (nearly) a float, and an inner fma
+// that adds the small lo terms to it would round them away in the same direction every
+// step, growing |w f| (twmul's imaginary part has that order; near +-pi/2 this one has
+// the weakness instead, which the phases of the modes that carry the norm do not reach).
+template <int DIR>
+__device__ __forceinline__ float2 phmul(float2 w, float4 f) {
+    const float fy = DIR < 0 ? f.y : -f.y, ly = DIR < 0 ? f.w : -f.w;
+    const float sr = fmaf(w.x, f.z, -w.y * ly);
+    const float si = fmaf(w.x, ly, w.y * f.z);
+    return mk(fmaf(w.x, f.x, fmaf(-w.y, fy, sr)), fmaf(w.y, f.x, fmaf(w.x, fy, si)));
+}
+template <int DIR>
+__device__ __forceinline__ double2 phmul(double2 w, double2 f) {
+    return twmul<DIR>(w, f);
+}
 // x * c for a compile-time constant c given in double: FP32 uses c_hi + c_lo, with the
 // small product x c_lo added inside the fma that forms the exact x c_hi, so the result is
 // x c rounded once.  (Rounding x c_hi first and adding x c_lo afterwards would lose the

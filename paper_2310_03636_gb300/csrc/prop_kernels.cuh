@@ -60,7 +60,7 @@ __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const t
     for (int m = 0; m < R; ++m) v[0][m] = row[t + m * TP];
     fft_pencil<N, R, -1, 1, Sync::Block>(v, xb, tws, t);
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[0][m] = twmul<-1>(v[0][m], ph[t + m * TP]);
+    for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
     fft_pencil<N, R, +1, 1, Sync::Block>(v, xb, tws, t);
 #pragma unroll
     for (int m = 0; m < R; ++m) row[t + m * TP] = v[0][m];
@@ -198,7 +198,7 @@ k_colpass(const PassArgs<T> a) {
     }
     if constexpr (MODE == kColK || MODE == kColKConj) {
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[0][m] = twmul<MODE == kColK ? -1 : +1>(v[0][m], a.ph[t + m * TP]);
+        for (int m = 0; m < R; ++m) v[0][m] = phmul<MODE == kColK ? -1 : +1>(v[0][m], a.ph[t + m * TP]);
         fft_pencil<N, R, +1, 1, Sync::Block>(v, buf, tws, t);
     }
 #pragma unroll
@@ -306,7 +306,7 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
         fft_pencil<N, R, -1, 1, Sync::Block>(v, xb, tws, t);
         if constexpr (!FWD_ONLY) {
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[0][m] = twmul<-1>(v[0][m], a.ph[t + m * TP]);
+            for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], a.ph[t + m * TP]);
             fft_pencil<N, R, +1, 1, Sync::Block>(v, xb, tws, t);
         }
 #pragma unroll
@@ -393,7 +393,7 @@ k_resident1d(const Res1DArgs<T> a) {
     for (int m = 0; m < R; ++m) {
         const twel<T> f = a.ph_half[t + m * TP];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
+        for (int c = 0; c < 3; ++c) v[c][m] = phmul<-1>(v[c][m], f);
     }
     fft_pencil<N, R, +1, 3, SY>(v, buf, tws, t);
     LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
@@ -413,7 +413,7 @@ k_resident1d(const Res1DArgs<T> a) {
         for (int m = 0; m < R; ++m) {
             const twel<T> f = ph[t + m * TP];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
+            for (int c = 0; c < 3; ++c) v[c][m] = phmul<-1>(v[c][m], f);
         }
         fft_pencil<N, R, +1, 3, SY>(v, buf, tws, t);
     }

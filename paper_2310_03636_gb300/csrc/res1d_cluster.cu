@@ -79,7 +79,7 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
         for (int m = 0; m < R; ++m) {
             const twel<T> f = ph[C * (t + m * TP) + rank];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][m] = twmul<-1>(v[c][m], f);
+            for (int c = 0; c < 3; ++c) v[c][m] = phmul<-1>(v[c][m], f);
         }
         fft_pencil<M, R, +1, 3, Sync::Block>(v, fb, tws, t);
         // publish z_rank, gather the inverse radix-C step for this block's sites
