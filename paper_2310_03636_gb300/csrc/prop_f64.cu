@@ -107,14 +107,13 @@ cudaError_t launch_colpass_tma<double>(int n, int axis, bool fwd_only, const CUt
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = n_tiles < kColCtasPerSm * sms ? n_tiles : kColCtasPerSm * sms;
 #define GPE_COLTMA(NN)                                                                                     \
     case NN: {                                                                                             \
         a.tw = tws[tw_slot<Tune<double>::kColR(NN)>()];                                                        \
-        if (axis == 2) return fwd_only ? colpass_tma_n<double, NN, true, true>(map, a, grid, s)                \
-                                       : colpass_tma_n<double, NN, false, true>(map, a, grid, s);              \
-        return fwd_only ? colpass_tma_n<double, NN, true, false>(map, a, grid, s)                              \
-                        : colpass_tma_n<double, NN, false, false>(map, a, grid, s);                            \
+        if (axis == 2) return fwd_only ? colpass_tma_n<double, NN, true, true>(map, a, sms, s)                \
+                                       : colpass_tma_n<double, NN, false, true>(map, a, sms, s);              \
+        return fwd_only ? colpass_tma_n<double, NN, true, false>(map, a, sms, s)                              \
+                        : colpass_tma_n<double, NN, false, false>(map, a, sms, s);                            \
     }
     switch (n) {
         GPE_COLTMA(64)

@@ -210,8 +210,6 @@ k_colpass(const PassArgs<T> a) {
 // loads tile i+1 while tile i is transformed, and stores each finished tile back through
 // the same tensor map.  ZPASS: pencils along z of a 3D map {2 nx, ny, nz 3 ntraj};
 // otherwise pencils along y of a 2D map {2 nx, rows}.  FWD_ONLY: forward FFT only.
-// Resident blocks per SM the persistent column pass is launched with.
-constexpr int kColCtasPerSm = 2;
 
 template <typename T>
 struct ColTmaArgs {
@@ -457,15 +455,31 @@ cudaError_t colpass_n(const PassArgs<T>& a, cudaStream_t s) {
     return launch_with_smem(k_colpass<T, N, R, COLS, MODE>, (int)grid, COLS * (N / R), smem, s, &a);
 }
 
+// The persistent column pass is launched with as many blocks as can be resident at once
+// (occupancy query, once per kernel): every SM holds the same number of blocks, each walks
+// the tiles with the grid stride.  At 512 (FP32) that is 3 blocks per SM with 80 registers
+// a thread; a 4th does not fit the shared memory.  More blocks than fit would run as a
+// second, partial wave.
 template <typename T, int N, bool FWD_ONLY, bool ZPASS>
-cudaError_t colpass_tma_n(const CUtensorMap& map, const ColTmaArgs<T>& a, int grid, cudaStream_t s) {
+cudaError_t colpass_tma_n(const CUtensorMap& map, const ColTmaArgs<T>& a, int sms, cudaStream_t s) {
     constexpr int R = Tune<T>::kColR(N);
     constexpr int COLS = Tune<T>::kColCols(N);
+    constexpr int THREADS = COLS * (N / R);
     const size_t smem = colpass_tma_smem<T, N, COLS>(R) + FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
     auto kern = k_colpass_tma<T, N, R, COLS, FWD_ONLY, ZPASS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, COLS * (N / R), smem, s>>>(map, a);
+    static const int per_sm = [&] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, THREADS, smem) != cudaSuccess) {
+            cudaGetLastError();
+            b = 1;
+        }
+        return b > 0 ? b : 1;
+    }();
+    const int cap = per_sm * sms;
+    const int grid = a.n_tiles < cap ? a.n_tiles : cap;
+    kern<<<grid, THREADS, smem, s>>>(map, a);
     return cudaGetLastError();
 }
 
