@@ -324,12 +324,11 @@ def test_own_sincos_against_cuda(B):
 
 
 @pytest.mark.parametrize("dtype,n,steps,tol", [("c128", 4096, 120, 1e-11), ("c128", 8192, 60, 1e-11),
-                                               ("c128", 16384, 40, 1e-11), ("c64", 8192, 100, 1e-4),
-                                               ("c64", 16384, 100, 1e-4), ("c64", 32768, 100, 1e-4)])
+                                               ("c128", 16384, 40, 1e-11), ("c64", 8192, 200, 1e-4),
+                                               ("c64", 16384, 200, 1e-4), ("c64", 32768, 200, 1e-4)])
 def test_cluster_1d(B, dtype, n, steps, tol):
-    """1D grids held by a thread-block cluster (radix-C step across the blocks).  FP32 is
-    checked at 100 steps: in long 1D boxes the dynamics amplify a rounding-size
-    perturbation ~160x over 200 steps (vs ~17x at N = 256), beyond what FP32 can meet."""
+    """1D grids held by a thread-block cluster (radix-C step across the blocks), FP32 at the
+    200-step bar."""
     ntraj, dt, seed = 2, 0.02, 13
     b = B.GPEBatch((n,), ntraj, dtype, C0, C1, Q, dt)
     b.init_noise(seed, MEAN, 0.5)
