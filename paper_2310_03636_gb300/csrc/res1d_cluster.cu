@@ -1,7 +1,7 @@
 // Resident 1D propagation of long grids on a thread-block cluster.
 //
 // A trajectory of N = C M points is held by a cluster of C blocks, block c owning the
-// contiguous sites [c M, (c+1) M) of all three components in registers for all steps.
+// contiguous sites [c M, (c+1) M) of all three components in shared memory for all steps.
 // The length-N transform splits as one radix-C step across the cluster and length-M
 // transforms inside each block (decimation in frequency):
 //   X[C k' + r] = FFT_M( y_r )[k'],   y_r[n'] = W_N^{n' r} sum_c x[n' + c M] W_C^{c r},
@@ -26,83 +26,79 @@ __device__ __forceinline__ V twc_rank(V a, int e) {
     return twc16<DIR>(a, (e * (16 / C)) & 15);
 }
 
+// Blocks per SM the cluster kernel is compiled for: as many as its shared memory allows.
+template <typename T, int M>
+constexpr int res1d_cluster_blocks() {
+    const int b = (227 * 1024) / (3 * smem_ld<T>(M) * (int)sizeof(cplx<T>) + 1024);
+    return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
+// Block ``rank`` keeps its slice [rank M, (rank+1) M) of the three components in shared
+// memory (element n of component c at buf[c LD + spad(n)]) for all steps; the kinetic step
+// handles one component at a time with its R points per thread in registers, so the kernel
+// stays small (the form holding all three components in registers was instruction-fetch
+// bound).  Per component: gather the radix-C inputs from every block, barrier (all reads
+// done before the slice is overwritten), local transforms and phase, publish z_rank,
+// barrier, gather the inverse radix-C step, barrier, store the new slice.
 template <typename T, int M, int R, int C>
-__global__ void __launch_bounds__(M / R)
+__global__ void __launch_bounds__(M / R, res1d_cluster_blocks<T, M>())
 k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, const twel<T>* __restrict__ wn) {
     using V = cplx<T>;
     constexpr int TP = M / R;
     constexpr int N = C * M;
     constexpr int LD = smem_ld<T>(M);
-    constexpr int TWN = FftPlan<M, R>::tw_size();
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     extern __shared__ __align__(128) unsigned char smraw[];
     V* buf = reinterpret_cast<V*>(smraw);                                  // [3][LD]
-    twel<T>* tws = reinterpret_cast<twel<T>*>(buf + tw_off<T>(3 * LD));
-    copy_table(tws, tw_local, TWN);
     const int t = threadIdx.x;
     const int traj = blockIdx.x / C;
-    V* base = a.ptrs[traj] + rank * M + t;
-    V* const fb[3] = {buf, buf + LD, buf + 2 * LD};
+    V* g = a.ptrs[traj] + rank * M;
     const V* rbuf[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) rbuf[c] = cl.map_shared_rank(buf, c);
-    V v[3][R];
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int m = 0; m < R; ++m) v[c][m] = base[c * N + m * TP];
-    __syncthreads();
+        for (int i = t; i < M; i += TP) buf[c * LD + spad(i)] = g[c * N + i];
 
     auto kinetic = [&](const twel<T>* __restrict__ ph) {
-        // publish this block's sites, gather the radix-C inputs of spectrum class ``rank``
+        cl.sync();   // every block's slices are final (loads, local step) before they are read
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            V v[1][R];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int m = 0; m < R; ++m) buf[c * LD + t + m * TP] = v[c][m];
-        cl.sync();
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const int n = t + m * TP;
-            const twel<T> w = wn[rank * M + n];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
+            for (int m = 0; m < R; ++m) {
+                const int n = t + m * TP;
                 V acc = mk((T)0, (T)0);
 #pragma unroll
-                for (int src = 0; src < C; ++src) acc = cadd(acc, twc_rank<C, -1>(rbuf[src][c * LD + n], src * rank));
-                v[c][m] = twmul<-1>(acc, w);
+                for (int src = 0; src < C; ++src) acc = cadd(acc, twc_rank<C, -1>(rbuf[src][c * LD + spad(n)], src * rank));
+                v[0][m] = twmul<-1>(acc, wn[rank * M + n]);
             }
-        }
-        cl.sync();
-        fft_pencil<M, R, -1, 3, Sync::Block>(v, fb, tws, t);
+            cl.sync();   // all reads of component c done before it is overwritten
+            V* const fb[1] = {buf + c * LD};
+            fft_pencil<M, R, -1, 1, Sync::Block>(v, fb, tw_local, t);
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const twel<T> f = ph[C * (t + m * TP) + rank];
+            for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[C * (t + m * TP) + rank]);
+            fft_pencil<M, R, +1, 1, Sync::Block>(v, fb, tw_local, t);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][m] = phmul<-1>(v[c][m], f);
-        }
-        fft_pencil<M, R, +1, 3, Sync::Block>(v, fb, tws, t);
-        // publish z_rank, gather the inverse radix-C step for this block's sites
+            for (int m = 0; m < R; ++m) buf[c * LD + spad(t + m * TP)] = v[0][m];
+            cl.sync();   // z_rank published
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int m = 0; m < R; ++m) buf[c * LD + t + m * TP] = v[c][m];
-        cl.sync();
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const int n = t + m * TP;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
+            for (int m = 0; m < R; ++m) {
+                const int n = t + m * TP;
                 V acc = mk((T)0, (T)0);
 #pragma unroll
                 for (int src = 0; src < C; ++src) {
-                    const V z = twmul<+1>(rbuf[src][c * LD + n], wn[src * M + n]);
+                    const V z = twmul<+1>(rbuf[src][c * LD + spad(n)], wn[src * M + n]);
                     acc = cadd(acc, twc_rank<C, +1>(z, src * rank));
                 }
-                v[c][m] = acc;
+                v[0][m] = acc;
             }
+            cl.sync();   // all reads of z done before the new slice replaces it
+#pragma unroll
+            for (int m = 0; m < R; ++m) buf[c * LD + spad(t + m * TP)] = v[0][m];
         }
-        cl.sync();
+        __syncthreads();
     };
 
     kinetic(a.ph_half);
@@ -110,25 +106,37 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
         if (a.vpot == nullptr) {
-#pragma unroll
-            for (int m = 0; m < R; ++m) local_step<T>(v[0][m], v[1][m], v[2][m], coef);
+#pragma unroll 2
+            for (int i = t; i < M; i += TP) {
+                const int k = spad(i);
+                V p1 = buf[k], p0 = buf[LD + k], pm = buf[2 * LD + k];
+                local_step<T>(p1, p0, pm, coef);
+                buf[k] = p1;
+                buf[LD + k] = p0;
+                buf[2 * LD + k] = pm;
+            }
         } else {
-#pragma unroll
-            for (int m = 0; m < R; ++m)
-                local_step<true, T>(v[0][m], v[1][m], v[2][m], coef, site_pot<T>(a.vpot, N, rank * M + t + m * TP));
+#pragma unroll 2
+            for (int i = t; i < M; i += TP) {
+                const int k = spad(i);
+                V p1 = buf[k], p0 = buf[LD + k], pm = buf[2 * LD + k];
+                local_step<true, T>(p1, p0, pm, coef, site_pot<T>(a.vpot, N, rank * M + i));
+                buf[k] = p1;
+                buf[LD + k] = p0;
+                buf[2 * LD + k] = pm;
+            }
         }
         kinetic(s == a.nsteps - 1 ? a.ph_half : a.ph_full);
     }
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int m = 0; m < R; ++m) base[c * N + m * TP] = v[c][m];
+        for (int i = t; i < M; i += TP) g[c * N + i] = buf[c * LD + spad(i)];
 }
 
 template <typename T, int M, int R, int C>
 cudaError_t res1d_cluster_n(const Res1DArgs<T>& a, const twel<T>* tw_local, const twel<T>* wn, cudaStream_t s) {
     auto kern = k_res1d_cluster<T, M, R, C>;
-    const size_t smem = (size_t)tw_off<T>(3 * smem_ld<T>(M)) * sizeof(cplx<T>) + FftPlan<M, R>::tw_size() * sizeof(twel<T>);
+    const size_t smem = (size_t)3 * smem_ld<T>(M) * sizeof(cplx<T>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
