@@ -1,7 +1,103 @@
-// Resident 1D kernel instantiations (whole trajectory on chip for all steps).
+// Resident 1D kernel: the whole trajectory on chip for all steps.
 #include "prop_kernels.cuh"
 
 namespace gpe {
+
+// Resident 1D: one block per trajectory; the field stays in shared memory for all steps
+// (three padded pencil buffers):
+//   K(dt/2) [L K(dt)]^(n-1) L K(dt/2).
+// Each component's transform holds its R points per thread in registers and exchanges
+// through the component's own buffer; the local step is a loop over the sites.  Keeping
+// one component in registers at a time, with the site loop not unrolled, keeps the kernel
+// small: a form with all three components in registers and every loop unrolled spent
+// most of its cycles waiting for instruction fetch at N = 4096 (255 registers, one block
+// per SM).  Stage twiddles and phases are read through L1.
+template <typename T, int N, int R, Sync SY>
+__device__ __forceinline__ void kinetic_resident(cplx<T>* const (&buf)[3], const twel<T>* __restrict__ tws,
+                                                 const twel<T>* __restrict__ ph, int t) {
+    using V = cplx<T>;
+    constexpr int TP = N / R;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        V v[1][R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[0][m] = buf[c][spad(t + m * TP)];
+        pencil_sync<SY>();   // every thread has its points before the first exchange overwrites
+        V* const b1[1] = {buf[c]};
+        fft_pencil<N, R, -1, 1, SY>(v, b1, tws, t);
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
+        fft_pencil<N, R, +1, 1, SY>(v, b1, tws, t);
+#pragma unroll
+        for (int m = 0; m < R; ++m) buf[c][spad(t + m * TP)] = v[0][m];
+    }
+    pencil_sync<SY>();
+}
+
+// Blocks per SM the resident kernel is compiled for: as many as its shared memory allows
+// (at most 8), so that the register budget does not cap them further.
+template <typename T, int N>
+constexpr int res1d_blocks() {
+    const int b = (227 * 1024) / (3 * smem_ld<T>(N) * (int)sizeof(cplx<T>) + 1024);
+    return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
+template <typename T, int N, int R>
+__global__ void __launch_bounds__(N / R, res1d_blocks<T, N>())
+k_resident1d(const Res1DArgs<T> a) {
+    using V = cplx<T>;
+    constexpr int TP = N / R;
+    constexpr int LD = smem_ld<T>(N);
+    constexpr Sync SY = (TP <= 32) ? Sync::Warp : Sync::Block;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    const twel<T>* tws = a.tw[tw_slot<R>()];
+    const int t = threadIdx.x;
+    V* g = a.ptrs[blockIdx.x];
+    V* const buf[3] = {sm, sm + LD, sm + 2 * LD};
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c)
+        for (int i = t; i < N; i += TP) buf[c][spad(i)] = g[c * N + i];
+    pencil_sync<SY>();
+    kinetic_resident<T, N, R, SY>(buf, tws, a.ph_half, t);
+    LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
+    for (int64_t s = 0; s < a.nsteps; ++s) {
+        coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
+        if (a.vpot == nullptr) {
+#pragma unroll 2
+            for (int i = t; i < N; i += TP) {
+                const int k = spad(i);
+                V p1 = buf[0][k], p0 = buf[1][k], pm = buf[2][k];
+                local_step<T>(p1, p0, pm, coef);
+                buf[0][k] = p1;
+                buf[1][k] = p0;
+                buf[2][k] = pm;
+            }
+        } else {
+#pragma unroll 2
+            for (int i = t; i < N; i += TP) {
+                const int k = spad(i);
+                V p1 = buf[0][k], p0 = buf[1][k], pm = buf[2][k];
+                local_step<true, T>(p1, p0, pm, coef, site_pot<T>(a.vpot, N, i));
+                buf[0][k] = p1;
+                buf[1][k] = p0;
+                buf[2][k] = pm;
+            }
+        }
+        pencil_sync<SY>();
+        kinetic_resident<T, N, R, SY>(buf, tws, (s == a.nsteps - 1) ? a.ph_half : a.ph_full, t);
+    }
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c)
+        for (int i = t; i < N; i += TP) g[c * N + i] = buf[c][spad(i)];
+}
+
+template <typename T, int N>
+cudaError_t resident1d_n(const Res1DArgs<T>& a, cudaStream_t s) {
+    constexpr int R = Tune<T>::kResR(N);
+    const size_t smem = (size_t)3 * smem_ld<T>(N) * sizeof(cplx<T>);
+    return launch_with_smem(k_resident1d<T, N, R>, a.ntraj, N / R, smem, s, &a);
+}
 
 template <> int resident1d_max_n<float>() { return 4096; }
 template <> int resident1d_max_n<double>() { return 2048; }
