@@ -307,6 +307,7 @@ def run_ours(args):
     e2e = {"value": su_per_step * k_e2e * ws / (e2e_ms * 1e-3), "unit": "site-updates/s",
            "h2d_bytes_per_step": int(b.psi.numel() * b.psi.element_size()),
            "d2h_bytes_per_step": int(sd * 8), "steps": k_e2e}
+    tiles = b.tiles(0)
     b.close()
 
     # plain FP64 comparator: one trajectory per launch, no graph
@@ -341,7 +342,8 @@ def run_ours(args):
                           "dt": WL.dt, "steps_per_bench_step": STEPS_PER_SAMPLE,
                           "observables_every": STEPS_PER_SAMPLE, "c0": WL.c0, "c1": WL.c1, "q": WL.q,
                           "parallelism": f"trajectories sharded over {ws} GPU(s)",
-                          "l2": "inputs larger than L2 (403 MB of fields per GPU)"},
+                          "l2": "inputs larger than L2 (403 MB of fields per GPU)",
+                          "column_tiles": {"y": tiles[0], "autotuned": tiles[2]}},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": launches, "fp64_plain": fp64, "status": status}
         print(json.dumps(out), flush=True)
@@ -351,9 +353,12 @@ def run_ours(args):
 
 
 def ncu_case():
-    """Short run of the benchmark workload for ncu captures: noise, 4 steps, one observables call."""
+    """Short run of the benchmark workload for ncu captures: noise, 4 steps, one observables call.
+    The tile autotuner is off here so that the captured launches are the workload's own
+    (the default width at 512 is the one the tuner keeps there; the bench line reports it)."""
     from paper_2310_03636_gb300 import binding as B
     b = B.GPEBatch(WL.shape, WL.ntraj, "c64", WL.c0, WL.c1, WL.q, WL.dt, dx=WL.dx)
+    b.set_autotune(False)
     b.init_noise(W.SEED_BASE, WL.mean_spinor(), WL.noise_per_mode)
     b.step(4)
     acc = b.new_accumulator(1)

@@ -96,8 +96,10 @@ gpe_status tw_init_noise(gpe_batch* batch, uint64_t seed, const double mean_spin
 
 /* Advances every trajectory by nsteps Strang steps of dt (Sec. 2.2 split-step scheme)
  * starting from the batch time, which then increases by nsteps dt.  The fields hold
- * psi(t) (not a half-kicked state) before and after the call.  Errors: GPE_EINVAL
- * (nsteps < 0). */
+ * psi(t) (not a half-kicked state) before and after the call.  The first call on an FP32
+ * batch also runs the tile autotuner (gpe_batch_set_autotune), which allocates a
+ * temporary scratch batch and synchronises the stream: make it before any stream capture
+ * of your own.  Errors: GPE_EINVAL (nsteps < 0). */
 gpe_status gpe_step_batch(gpe_batch* batch, int64_t nsteps, void* stream);
 
 /* Observable flags. */
@@ -177,6 +179,20 @@ gpe_status gpe_batch_set_integrator(gpe_batch* batch, int32_t kind);
  * nsteps before any stream capture of your own.  Disabled by default; ignored while
  * profiling is enabled. */
 gpe_status gpe_batch_set_graph(gpe_batch* batch, int32_t enable);
+
+/* Tile autotuner of the strided (y, z) kinetic passes (the paper prescribes none; the
+ * choice changes no result bit).  Enabled by default: the first gpe_step_batch call of an
+ * FP32 batch times, per shape group with back-to-back fields, every tile width (complex
+ * columns per block) the pass is built for on a zero-filled scratch batch of the group's
+ * shape (at most 256 MiB, freed again; if it cannot be allocated the defaults stay) and
+ * keeps the fastest per axis.  Skipped while the stream is being captured.  Disabled, or
+ * for FP64 and non-contiguous groups, fixed per-size defaults are used. */
+gpe_status gpe_batch_set_autotune(gpe_batch* batch, int32_t enable);
+
+/* Tile widths in use for trajectory traj's group: cols[0] for y, cols[1] for z (0 where the
+ * group has no such pass or uses the non-tensor-map pass), *tuned = 1 once the autotuner
+ * has run for the group (tuned may be NULL).  Errors: GPE_EINVAL. */
+gpe_status gpe_batch_get_tiles(const gpe_batch* batch, int32_t traj, int32_t cols[2], int32_t* tuned);
 
 /* Batch time as a step count (t = step * dt); settable for replaying segments. */
 int64_t gpe_batch_get_step(const gpe_batch* batch);

@@ -65,6 +65,8 @@ def _load():
         "gpe_batch_set_integrator": ([vp, i32], ctypes.c_int),
         "gpe_batch_set_traj_base": ([vp, i64], ctypes.c_int),
         "gpe_batch_set_potential": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
+        "gpe_batch_set_autotune": ([vp, i32], ctypes.c_int),
+        "gpe_batch_get_tiles": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
         "gpe_batch_set_mean_field": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_diagnostics_noalloc": ([vp, i32, i32, ctypes.POINTER(i32), dbl, ctypes.c_int, dbl, dbl, dbl, vp, vp],
@@ -309,6 +311,16 @@ class GPEBatch:
 
     def set_graph(self, enable=True):
         _check(LIB.gpe_batch_set_graph(self.h, 1 if enable else 0))
+
+    def set_autotune(self, enable=True):
+        _check(LIB.gpe_batch_set_autotune(self.h, 1 if enable else 0))
+
+    def tiles(self, traj=0):
+        """(cols_y, cols_z, tuned) of the column passes of trajectory traj's group."""
+        cols = (ctypes.c_int32 * 2)()
+        tuned = ctypes.c_int32()
+        _check(LIB.gpe_batch_get_tiles(self.h, int(traj), cols, ctypes.byref(tuned)))
+        return int(cols[0]), int(cols[1]), bool(tuned.value)
 
     def set_potential(self, V, shape=None):
         """V_m(x) for the trajectories on grid ``shape`` (default: the batch's first shape).

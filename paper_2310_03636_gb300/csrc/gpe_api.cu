@@ -89,31 +89,36 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Tensor maps over a contiguous group: y pencils through a 2D view {2 nx, ntraj 3 nz ny}
 // of the whole batch, z pencils through a 3D view {2 nx, ny, nz 3 ntraj}; boxes are
 // COLS complex columns wide and min(n, 256) points long.
-bool gpe::encode_group_maps(Group& g, int eb, int cols_y, int cols_z) {
+bool gpe::encode_maps(CUtensorMap* map_y, CUtensorMap* map_z, const Group& g, void* base, int ntraj, int eb,
+                      int cols_y, int cols_z) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || g.ndim < 2) return false;
     const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     const cuuint64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const cuuint32_t es[3] = {1, 1, 1};
     {
-        const cuuint64_t dims[2] = {2 * nx, (cuuint64_t)g.ntraj * 3 * nz * ny};
+        const cuuint64_t dims[2] = {2 * nx, (cuuint64_t)ntraj * 3 * nz * ny};
         const cuuint64_t strides[1] = {2 * nx * (cuuint64_t)eb};
         const cuuint32_t box[2] = {(cuuint32_t)(2 * cols_y), (cuuint32_t)(ny < 256 ? ny : 256)};
-        if (enc(&g.map_y, dt, 2, g.hptrs[0], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        if (enc(map_y, dt, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
     }
     if (g.ndim == 3) {
-        const cuuint64_t dims[3] = {2 * nx, ny, nz * 3 * (cuuint64_t)g.ntraj};
+        const cuuint64_t dims[3] = {2 * nx, ny, nz * 3 * (cuuint64_t)ntraj};
         const cuuint64_t strides[2] = {2 * nx * (cuuint64_t)eb, 2 * nx * ny * (cuuint64_t)eb};
         const cuuint32_t box[3] = {(cuuint32_t)(2 * cols_z), 1, (cuuint32_t)(nz < 256 ? nz : 256)};
-        if (enc(&g.map_z, dt, 3, g.hptrs[0], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        if (enc(map_z, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
     }
     return true;
+}
+
+bool gpe::encode_group_maps(Group& g, int eb) {
+    return encode_maps(&g.map_y, &g.map_z, g, g.hptrs[0], g.ntraj, eb, g.cols[1], g.ndim == 3 ? g.cols[2] : g.cols[1]);
 }
 
 struct gpe_batch {
@@ -125,6 +130,7 @@ struct gpe_batch {
     std::vector<Group> groups;
     int64_t step = 0;
     int integrator = 0;               // GPE_INTEGRATOR_PAPER or GPE_INTEGRATOR_ROTATION
+    bool autotune = true;             // time the column-pass tile widths on the first step
     int64_t traj_base = 0;            // added to batch indices in the noise counter
     int* d_status = nullptr;
     int device = 0;
@@ -329,12 +335,12 @@ cudaError_t col_pass(gpe_batch* b, const Group& g, int ax, bool half, cudaStream
     ProfScope ps(b, 1, s, 1);
     if (g.contiguous) {
         const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-        const int nxt = nx / colpass_cols<T>(g.n[ax]);
+        const int nxt = nx / g.cols[ax];
         const int n_tiles = ax == 1 ? nxt * g.ntraj * 3 * nz : nxt * ny * g.ntraj * 3;
         const twel<T>* tws[3] = {reinterpret_cast<const twel<T>*>(g.tw[ax][0]),
                                  reinterpret_cast<const twel<T>*>(g.tw[ax][1]),
                                  reinterpret_cast<const twel<T>*>(g.tw[ax][2])};
-        return launch_colpass_tma<T>(g.n[ax], ax, false, ax == 1 ? g.map_y : g.map_z, n_tiles, nxt, ny, tws,
+        return launch_colpass_tma<T>(g.n[ax], ax, g.cols[ax], ax == 1 ? g.map_y : g.map_z, n_tiles, nxt, ny, tws,
                                      reinterpret_cast<const twel<T>*>(half ? g.ph_half[ax] : g.ph_full[ax]),
                                      b->d_status, s);
     }
@@ -416,6 +422,85 @@ gpe_status step_group(gpe_batch* b, const Group& g, int64_t nsteps, cudaStream_t
 void drop_graphs(gpe_batch* b) {
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second.exec);
     b->graphs.clear();
+}
+
+// Column-pass tile autotuner.  On the first step of an FP32 batch, every contiguous shape
+// group times each tile width the column pass is built for (colpass_tma_candidates) on a
+// scratch batch shaped like its own fields -- up to 256 MiB, zero-filled: the pass's cost
+// does not depend on the values -- one warm-up and three timed launches per candidate on
+// the caller's stream, keeps the fastest per axis, frees the scratch and re-encodes the
+// group's tensor maps.  The width changes no result bit.  Skipped while the stream is
+// being captured (the defaults stay) or when disabled.
+gpe_status tune_tiles(gpe_batch* b, cudaStream_t s) {
+    if (!b->autotune || b->dtype != GPE_C64) return GPE_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return GPE_OK;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return GPE_OK;
+    for (Group& g : b->groups) {
+        if (g.tuned || !g.contiguous || g.ndim < 2) continue;
+        g.tuned = true;
+        const size_t per_traj = (size_t)3 * g.sites * sizeof(float2);
+        const size_t cap = ((size_t)256 << 20) / per_traj;
+        const int nt = (int)std::min<size_t>((size_t)g.ntraj, cap < 1 ? 1 : cap);
+        void* scratch = nullptr;
+        if (cudaMalloc(&scratch, per_traj * nt) != cudaSuccess) {
+            cudaGetLastError();
+            continue;   // no room to tune: keep the defaults
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        bool ok = cudaMemsetAsync(scratch, 0, per_traj * nt, s) == cudaSuccess &&
+                  cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+        for (int ax = 1; ok && ax < g.ndim; ++ax) {
+            int cand[8];
+            const int nc = colpass_tma_candidates<float>(g.n[ax], cand);
+            float best = 0.f;
+            int best_c = g.cols[ax];
+            const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+            const twel<float>* tws[3] = {reinterpret_cast<const twel<float>*>(g.tw[ax][0]),
+                                         reinterpret_cast<const twel<float>*>(g.tw[ax][1]),
+                                         reinterpret_cast<const twel<float>*>(g.tw[ax][2])};
+            const twel<float>* ph = reinterpret_cast<const twel<float>*>(g.ph_full[ax]);
+            for (int i = 0; i < nc; ++i) {
+                const int c = cand[i];
+                if (nx % c) continue;
+                CUtensorMap my{}, mz{};
+                if (!encode_maps(&my, &mz, g, scratch, nt, 4, c, c)) continue;
+                const int nxt = nx / c;
+                const int n_tiles = ax == 1 ? nxt * nt * 3 * nz : nxt * ny * nt * 3;
+                auto launch = [&]() {
+                    return launch_colpass_tma<float>(g.n[ax], ax, c, ax == 1 ? my : mz, n_tiles, nxt, ny, tws, ph,
+                                                     b->d_status, s);
+                };
+                if (launch() != cudaSuccess) {   // does not fit (shared memory): not a candidate here
+                    cudaGetLastError();
+                    continue;
+                }
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 3; ++r) launch();
+                cudaEventRecord(e1, s);
+                g_launches += 4;
+                float ms = 0.f;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                if (best == 0.f || ms < best) {
+                    best = ms;
+                    best_c = c;
+                }
+            }
+            g.cols[ax] = best_c;
+        }
+        cudaStreamSynchronize(s);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(scratch);
+        if (!encode_group_maps(g, 4)) return fail(GPE_ECUDA, "tensor maps after tile tuning");
+    }
+    return GPE_OK;
 }
 
 // All groups advance nsteps; with several groups each runs on its own stream, forked
@@ -527,10 +612,9 @@ gpe_status gpe_batch_create(const gpe_traj* trajs, int32_t ntraj, gpe_dtype dtyp
         for (int i = 1; i < g.ntraj && contiguous; ++i)
             contiguous = (char*)g.hptrs[i] == (char*)g.hptrs[0] + (size_t)i * 3 * g.sites * vb;
         if (contiguous) {
-            const int cy = (dtype == GPE_C64) ? colpass_cols<float>(g.n[1]) : colpass_cols<double>(g.n[1]);
-            const int cz = g.ndim == 3 ? ((dtype == GPE_C64) ? colpass_cols<float>(g.n[2]) : colpass_cols<double>(g.n[2]))
-                                       : cy;
-            contiguous = encode_group_maps(g, (int)(vb / 2), cy, cz);
+            for (int ax = 1; ax < g.ndim; ++ax)
+                g.cols[ax] = (dtype == GPE_C64) ? colpass_cols<float>(g.n[ax]) : colpass_cols<double>(g.n[ax]);
+            contiguous = encode_group_maps(g, (int)(vb / 2));
         }
         g.contiguous = contiguous;
     }
@@ -607,6 +691,10 @@ gpe_status gpe_step_batch(gpe_batch* b, int64_t nsteps, void* stream) {
     if (nsteps < 0) return fail(GPE_EINVAL, "nsteps < 0");
     if (nsteps == 0) return GPE_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    {
+        gpe_status ts = tune_tiles(b, s);
+        if (ts != GPE_OK) return ts;
+    }
     if (b->graph_mode && b->p.n_knots == 0 && !b->prof.on) {
         auto it = b->graphs.find(nsteps);
         if (it == b->graphs.end()) {
@@ -918,6 +1006,25 @@ gpe_status gpe_batch_set_mean_field(gpe_batch* b, const int32_t n[3], const doub
     if (for_shape(b, n, [&](Group& g) { g.mean_field = mean_field; }) == 0)
         return fail(GPE_EINVAL, "no trajectories of shape %d x %d x %d", n[0], n[1], n[2]);
     return GPE_OK;
+}
+
+gpe_status gpe_batch_set_autotune(gpe_batch* b, int32_t enable) {
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    b->autotune = enable != 0;
+    return GPE_OK;
+}
+
+gpe_status gpe_batch_get_tiles(const gpe_batch* b, int32_t traj, int32_t cols[2], int32_t* tuned) {
+    if (!b || !cols || traj < 0 || traj >= (int32_t)b->trajs.size()) return fail(GPE_EINVAL, "bad batch or trajectory");
+    for (const Group& g : b->groups)
+        for (int id : g.ids)
+            if (id == traj) {
+                cols[0] = g.contiguous ? g.cols[1] : 0;
+                cols[1] = g.contiguous && g.ndim == 3 ? g.cols[2] : 0;
+                if (tuned) *tuned = g.tuned ? 1 : 0;
+                return GPE_OK;
+            }
+    return fail(GPE_EINVAL, "trajectory %d not found", traj);
 }
 
 gpe_status gpe_batch_set_graph(gpe_batch* b, int32_t enable) {

@@ -85,6 +85,8 @@ struct Group {
     void* wn = nullptr;            // cluster 1D: W_N^{n r}, r < cluster, n < M
     CUtensorMap map_y{};           // 2D map {2 nx, ntraj 3 nz ny} of the batch (ndim >= 2)
     CUtensorMap map_z{};           // 3D map {2 nx, ny, nz 3 ntraj} (ndim == 3)
+    int cols[3] = {0, 0, 0};       // column-pass tile width per axis (1: y, 2: z)
+    bool tuned = false;            // tile widths chosen by timing
     const void* vpot = nullptr;    // caller's potential [3][sites] (real, the batch's precision), or null
     const double* mean_field = nullptr;   // caller's initial mean field [3][sites] complex FP64, or null
 };
@@ -112,12 +114,20 @@ template <typename T>
 cudaError_t launch_rowfft(int n, cplx<T>* data, int64_t rows, const twel<T>* const* tw, cudaStream_t s, int dir = -1);
 template <typename T>
 int colpass_cols(int n);
-// Persistent TMA column pass over a contiguous group: axis 1 (y) or 2 (z).
+// Persistent TMA column pass over a contiguous group: axis 1 (y) or 2 (z), tiles ``cols``
+// complex columns wide (one of colpass_tma_candidates; the map's box must match).
 template <typename T>
-cudaError_t launch_colpass_tma(int n, int axis, bool fwd_only, const CUtensorMap& map, int n_tiles, int nx_tiles,
+cudaError_t launch_colpass_tma(int n, int axis, int cols, const CUtensorMap& map, int n_tiles, int nx_tiles,
                                int ny, const twel<T>* tw4_8_16[3], const twel<T>* ph, int* status, cudaStream_t s);
-// Encodes the tensor maps of a contiguous group (elements of ``elem_bytes`` per real).
-bool encode_group_maps(Group& g, int elem_bytes, int cols_y, int cols_z);
+// Tile widths the column pass is built for at pencil length n (written to cols[0..]).
+template <typename T>
+int colpass_tma_candidates(int n, int* cols);
+// Tensor maps for the column passes of a group's shape over ntraj fields stored back to
+// back from base (elements of ``elem_bytes`` per real), boxes cols_y / cols_z wide.
+bool encode_maps(CUtensorMap* map_y, CUtensorMap* map_z, const Group& g, void* base, int ntraj, int elem_bytes,
+                 int cols_y, int cols_z);
+// Encodes the group's own maps with its current tile widths.
+bool encode_group_maps(Group& g, int elem_bytes);
 template <typename T>
 cudaError_t launch_resident1d(int n, const Res1DArgs<T>& a, cudaStream_t s);
 template <typename T>

@@ -95,35 +95,5 @@ cudaError_t launch_rowfft<float>(int n, cplx<float>* d, int64_t rows, const twel
 
 namespace gpe {
 
-template <>
-cudaError_t launch_colpass_tma<float>(int n, int axis, bool fwd_only, const CUtensorMap& map, int n_tiles, int nx_tiles,
-                                  int ny, const twel<float>* tws[3], const twel<float>* ph, int* status, cudaStream_t s) {
-    ColTmaArgs<float> a{};
-    a.n_tiles = n_tiles;
-    a.nx_tiles = nx_tiles;
-    a.ny = ny;
-    a.ph = ph;
-    a.status = status;
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-#define GPE_COLTMA(NN)                                                                                     \
-    case NN: {                                                                                             \
-        a.tw = tws[tw_slot<Tune<float>::kColR(NN)>()];                                                        \
-        if (axis == 2) return fwd_only ? colpass_tma_n<float, NN, true, true>(map, a, sms, s)                \
-                                       : colpass_tma_n<float, NN, false, true>(map, a, sms, s);              \
-        return fwd_only ? colpass_tma_n<float, NN, true, false>(map, a, sms, s)                              \
-                        : colpass_tma_n<float, NN, false, false>(map, a, sms, s);                            \
-    }
-    switch (n) {
-        GPE_COLTMA(64)
-        GPE_COLTMA(128)
-        GPE_COLTMA(256)
-        GPE_COLTMA(512)
-        GPE_COLTMA(1024)
-        default: return cudaErrorInvalidValue;
-    }
-#undef GPE_COLTMA
-}
 
 }  // namespace gpe

@@ -96,8 +96,16 @@ cudaError_t launch_rowfft<double>(int n, cplx<double>* d, int64_t rows, const tw
 namespace gpe {
 
 template <>
-cudaError_t launch_colpass_tma<double>(int n, int axis, bool fwd_only, const CUtensorMap& map, int n_tiles, int nx_tiles,
-                                  int ny, const twel<double>* tws[3], const twel<double>* ph, int* status, cudaStream_t s) {
+int colpass_tma_candidates<double>(int n, int* cols) {
+    cols[0] = Tune<double>::kColCols(n);
+    return 1;
+}
+
+template <>
+cudaError_t launch_colpass_tma<double>(int n, int axis, int cols, const CUtensorMap& map, int n_tiles, int nx_tiles,
+                                       int ny, const twel<double>* tws[3], const twel<double>* ph, int* status,
+                                       cudaStream_t s) {
+    if (cols != Tune<double>::kColCols(n)) return cudaErrorInvalidValue;
     ColTmaArgs<double> a{};
     a.n_tiles = n_tiles;
     a.nx_tiles = nx_tiles;
@@ -109,11 +117,10 @@ cudaError_t launch_colpass_tma<double>(int n, int axis, bool fwd_only, const CUt
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 #define GPE_COLTMA(NN)                                                                                     \
     case NN: {                                                                                             \
-        a.tw = tws[tw_slot<Tune<double>::kColR(NN)>()];                                                        \
-        if (axis == 2) return fwd_only ? colpass_tma_n<double, NN, true, true>(map, a, sms, s)                \
-                                       : colpass_tma_n<double, NN, false, true>(map, a, sms, s);              \
-        return fwd_only ? colpass_tma_n<double, NN, true, false>(map, a, sms, s)                              \
-                        : colpass_tma_n<double, NN, false, false>(map, a, sms, s);                            \
+        constexpr int C = Tune<double>::kColCols(NN);                                                      \
+        a.tw = tws[tw_slot<Tune<double>::kColR(NN)>()];                                                    \
+        if (axis == 2) return colpass_tma_n<double, NN, C, false, true>(map, a, sms, s);                   \
+        return colpass_tma_n<double, NN, C, false, false>(map, a, sms, s);                                 \
     }
     switch (n) {
         GPE_COLTMA(64)

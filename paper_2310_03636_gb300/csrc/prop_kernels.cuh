@@ -401,10 +401,9 @@ cudaError_t colpass_n(const PassArgs<T>& a, cudaStream_t s) {
 // the tiles with the grid stride.  At 512 (FP32) that is 3 blocks per SM with 80 registers
 // a thread; a 4th does not fit the shared memory.  More blocks than fit would run as a
 // second, partial wave.
-template <typename T, int N, bool FWD_ONLY, bool ZPASS>
+template <typename T, int N, int COLS, bool FWD_ONLY, bool ZPASS>
 cudaError_t colpass_tma_n(const CUtensorMap& map, const ColTmaArgs<T>& a, int sms, cudaStream_t s) {
     constexpr int R = Tune<T>::kColR(N);
-    constexpr int COLS = Tune<T>::kColCols(N);
     constexpr int THREADS = COLS * (N / R);
     const size_t smem = colpass_tma_smem<T, N, COLS>(R) + FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
     auto kern = k_colpass_tma<T, N, R, COLS, FWD_ONLY, ZPASS>;

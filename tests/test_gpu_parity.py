@@ -421,3 +421,23 @@ def test_full_size_3d_256_sampled(B):
     N0 = d0[:, :3].sum(1)
     assert np.abs(d1[:, :3].sum(1) - N0).max() < 1e-5 * N0.max()
     b.close()
+
+
+@pytest.mark.parametrize("shape,ntraj", [((256, 256), 4), ((64, 128, 64), 2), ((128, 1024), 2)])
+def test_autotuned_tiles_change_no_bit(B, shape, ntraj):
+    """The column-pass tile widths the autotuner picks are among the built candidates, and
+    the fields are bitwise the same as with the fixed default widths."""
+    out = []
+    for tune in (False, True):
+        b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, 0.02)
+        b.set_autotune(tune)
+        b.init_noise(21, MEAN, 0.5)
+        b.step(7)
+        b.step(5)
+        assert b.sync_status() == B.GPE_OK
+        cy, cz, tuned = b.tiles(0)
+        assert tuned == tune
+        assert cy in (2, 4, 8, 16) and (cz in (2, 4, 8, 16) if len(shape) == 3 else cz == 0)
+        out.append(b.psi.cpu().numpy())
+        b.close()
+    np.testing.assert_array_equal(out[0], out[1])
