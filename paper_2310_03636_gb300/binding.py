@@ -248,7 +248,17 @@ class GPEBatch:
         self.dx, self.dt, self.c0, self.c1, self.q = dx, dt, c0, c1, q
         if isinstance(shape, (list,)) and shape and isinstance(shape[0], (tuple, list)):
             self.shapes = [tuple(s) for s in shape]
-            self.psi = [torch.zeros((3,) + s, dtype=tdt, device=device) for s in self.shapes]
+            # trajectories of one shape share one allocation, back to back, so that the
+            # library can use its tensor-map passes (and tune their tiles) for the group
+            self._blocks = {}
+            for s in dict.fromkeys(self.shapes):
+                cnt = self.shapes.count(s)
+                self._blocks[s] = torch.zeros((cnt, 3) + s, dtype=tdt, device=device)
+            used = {s: 0 for s in self._blocks}
+            self.psi = []
+            for s in self.shapes:
+                self.psi.append(self._blocks[s][used[s]])
+                used[s] += 1
             trajs = [(s, dx, p) for s, p in zip(self.shapes, self.psi)]
             self.uniform = False
         else:
