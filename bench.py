@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", choices=["2d", "1d", "3d", "ragged", "adjoint"], default="2d",
+    p.add_argument("--workload", choices=["2d", "1d", "3d", "ragged", "adjoint", "paper1d", "paper1d_f64"], default="2d",
                    help="2d: the benchmark workload (default); others print a line for that configuration")
     p.add_argument("--ncu-case", action="store_true",
                    help="small profiling target: the 512^2 x 64 batch (403 MB > L2), 4 steps + observables")
@@ -397,6 +397,16 @@ def run_other(args):
         su = sum(int(np.prod(sh)) for sh in shapes) * 3 * per
         name, dtype = "ragged_200x1d_1k-16k_32x2d_128-1024_c64", "f32"
         extra["trajectories"] = len(shapes)
+    elif args.workload in ("paper1d", "paper1d_f64"):
+        # the paper's 1D grid (Sec. 2.2: 4096 points, three components), many runs at once
+        f64 = args.workload == "paper1d_f64"
+        ntraj = 304 if f64 else 3040
+        b = B.GPEBatch((4096,), ntraj, "c128" if f64 else "c64", 1.0, -0.1, 0.09, 0.04)
+        per, flags = (200 if f64 else 1000), 0
+        su = 4096 * 3 * ntraj * per
+        name, dtype = f"1d_4096_{'c128' if f64 else 'c64'}_{ntraj}traj", "f64" if f64 else "f32"
+        extra["paper_context"] = ("paper: 4096 points, FP64, V100/A100, one 1.5e6-step run in 120-150 s "
+                                  "with many runs per GPU (Sec. 2.2); not the same configuration")
     else:
         return run_adjoint(args)
     nb, sd = b.layout()
