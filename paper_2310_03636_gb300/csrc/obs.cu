@@ -66,6 +66,10 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV * 32
     __syncthreads();
 }
 
+// Per-site terms are formed in the fields' precision and summed per thread in it (16
+// sites per thread), the per-thread partials then reduced in FP64 in a fixed order: for
+// FP32 fields the per-site FP64 arithmetic cost far more than the read of the fields, and
+// the partials carry the FP32 fields' own relative precision.  FP64 fields stay FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_obs_prep(cplx<T>* const* __restrict__ ptrs, int t0, cplx<T>* __restrict__ W, int64_t sites, double c0,
@@ -75,31 +79,37 @@ k_obs_prep(cplx<T>* const* __restrict__ ptrs, int t0, cplx<T>* __restrict__ W, i
     const int tl = blockIdx.y;
     const V* f = ptrs[t0 + tl];
     V* w = W + (int64_t)tl * 4 * sites;
-    double acc[kPartVals] = {0, 0, 0, 0, 0, 0, 0};
+    // n_1, n_0, n_-1, n_1 + n_-1, rho^2, F_z^2 + |F_perp|^2, sum_m V_m n_m
+    T pt[kPartVals] = {0, 0, 0, 0, 0, 0, 0};
     const int64_t s0 = (int64_t)blockIdx.x * kSitesPerBlock;
+    const T s2 = (T)1.41421356237309504880;
     for (int k = 0; k < kSitesPerBlock / kThreads; ++k) {
         const int64_t i = s0 + k * kThreads + threadIdx.x;
         if (i >= sites) break;
         const V p1 = f[i], p0 = f[sites + i], pm = f[2 * sites + i];
-        const double a1r = p1.x, a1i = p1.y, a0r = p0.x, a0i = p0.y, amr = pm.x, ami = pm.y;
-        const double n1 = a1r * a1r + a1i * a1i, n0 = a0r * a0r + a0i * a0i, nm = amr * amr + ami * ami;
-        const double rho = n1 + n0 + nm, fz = n1 - nm;
+        const T n1 = cabs2(p1), n0 = cabs2(p0), nm = cabs2(pm);
+        const T rho = n1 + n0 + nm, fz = n1 - nm;
         // F_perp = sqrt2 (conj(p1) p0 + conj(p0) pm)
-        const double s2 = 1.41421356237309504880;
-        const double fr = s2 * ((a1r * a0r + a1i * a0i) + (a0r * amr + a0i * ami));
-        const double fi = s2 * ((a1r * a0i - a1i * a0r) + (a0r * ami - a0i * amr));
-        acc[0] += n1;
-        acc[1] += n0;
-        acc[2] += nm;
-        acc[3] += q * (n1 + nm);
-        acc[4] += 0.5 * c0 * rho * rho;
-        acc[5] += 0.5 * c1 * (fz * fz + fr * fr + fi * fi);
-        if (vpot) acc[6] += (double)vpot[i] * n1 + (double)vpot[sites + i] * n0 + (double)vpot[2 * sites + i] * nm;
+        const T fr = s2 * ((p1.x * p0.x + p1.y * p0.y) + (p0.x * pm.x + p0.y * pm.y));
+        const T fi = s2 * ((p1.x * p0.y - p1.y * p0.x) + (p0.x * pm.y - p0.y * pm.x));
+        pt[0] += n1;
+        pt[1] += n0;
+        pt[2] += nm;
+        pt[3] += n1 + nm;
+        pt[4] += rho * rho;
+        pt[5] += fz * fz + fr * fr + fi * fi;
+        if (vpot) pt[6] += vpot[i] * n1 + vpot[sites + i] * n0 + vpot[2 * sites + i] * nm;
         w[i] = p1;
         w[sites + i] = p0;
         w[2 * sites + i] = pm;
-        w[3 * sites + i] = mk((T)fr, (T)fi);
+        w[3 * sites + i] = mk(fr, fi);
     }
+    double acc[kPartVals];
+#pragma unroll
+    for (int k = 0; k < kPartVals; ++k) acc[k] = (double)pt[k];
+    acc[3] *= q;
+    acc[4] *= 0.5 * c0;
+    acc[5] *= 0.5 * c1;
     block_sum<kPartVals>(acc, sm);
     if (threadIdx.x == 0) {
         double* o = part + ((int64_t)tl * nblk + blockIdx.x) * kPartVals;
@@ -108,30 +118,32 @@ k_obs_prep(cplx<T>* const* __restrict__ ptrs, int t0, cplx<T>* __restrict__ W, i
     }
 }
 
+// Kinetic energy partials: sum over a block's modes of (k^2 / 2) |psi_m(k)|^2, mode
+// coordinates from shifts (all extents are powers of two), terms in the fields' precision.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_obs_ekin(const cplx<T>* __restrict__ W, int64_t sites, int nx, int ny, int nz, double dx,
+k_obs_ekin(const cplx<T>* __restrict__ W, int64_t sites, int lx, int ly, int nz, double dx,
            double* __restrict__ ekin, int64_t nblk) {
     using V = cplx<T>;
     __shared__ double sm[32];
+    const int nx = 1 << lx, ny = 1 << ly;
     const int tl = blockIdx.z, c = blockIdx.y;
     const V* w = W + ((int64_t)tl * 4 + c) * sites;
     const double two_pi = 6.283185307179586476925286766559;
-    const double gx = two_pi / (nx * dx), gy = two_pi / (ny * dx), gz = two_pi / (nz * dx);
-    double acc[1] = {0.0};
+    const T gx = (T)(two_pi / (nx * dx)), gy = (T)(two_pi / (ny * dx)), gz = (T)(two_pi / (nz * dx));
+    T pt = 0;
     const int64_t s0 = (int64_t)blockIdx.x * kSitesPerBlock;
     for (int k = 0; k < kSitesPerBlock / kThreads; ++k) {
         const int64_t i = s0 + k * kThreads + threadIdx.x;
         if (i >= sites) break;
-        const int ix = (int)(i % nx);
-        const int iy = (int)((i / nx) % ny);
-        const int iz = (int)(i / ((int64_t)nx * ny));
-        const int jx = fold(ix, nx), jy = fold(iy, ny), jz = fold(iz, nz);
-        const double kx = gx * jx, ky = gy * jy, kz = gz * jz;
+        const int ix = (int)(i & (nx - 1));
+        const int iy = (int)((i >> lx) & (ny - 1));
+        const int iz = (int)(i >> (lx + ly));
+        const T kx = gx * (T)fold(ix, nx), ky = gy * (T)fold(iy, ny), kz = gz * (T)fold(iz, nz);
         const V a = w[i];
-        const double p = (double)a.x * a.x + (double)a.y * a.y;
-        acc[0] += 0.5 * (kx * kx + ky * ky + kz * kz) * p;
+        pt += (kx * kx + ky * ky + kz * kz) * cabs2(a);
     }
+    double acc[1] = {0.5 * (double)pt};
     block_sum<1>(acc, sm);
     if (threadIdx.x == 0) ekin[((int64_t)tl * 3 + c) * nblk + blockIdx.x] = acc[0];
 }
@@ -270,7 +282,10 @@ gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q,
             if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs strided fft", e);
         }
         if (flags & GPE_OBS_DIAG) {
-            k_obs_ekin<T><<<dim3((unsigned)nblk, 3, nc), kThreads, 0, s>>>(W, g.sites, g.n[0], g.n[1], g.n[2], g.dx,
+            int lx = 0, ly = 0;
+            while ((1 << lx) < g.n[0]) ++lx;
+            while ((1 << ly) < g.n[1]) ++ly;
+            k_obs_ekin<T><<<dim3((unsigned)nblk, 3, nc), kThreads, 0, s>>>(W, g.sites, lx, ly, g.n[2], g.dx,
                                                                           w.d_ekin, w.nblk);
             k_obs_final<<<nc, kThreads, 0, s>>>(w.d_part, w.d_ekin, w.nblk, nblk, g.d_ids, t0, vol, 1.0 / (double)g.sites,
                                                 acc_slot + 4 * (int64_t)(w.nbins > 0 ? w.nbins : 0), d_status);

@@ -25,7 +25,7 @@ def B():
 
 @pytest.mark.parametrize("dtype,shape,ntraj,dx,tol", [
     ("c128", (128, 128), 3, 0.8, 1e-10),
-    ("c64", (512, 512), 5, 1.0, 1e-10),
+    ("c64", (512, 512), 5, 1.0, 1e-6),      # the batch API sums FP32 fields' terms in FP32 per thread
     ("c128", (2048,), 2, 0.5, 1e-10),
 ])
 def test_noalloc_matches_observables(B, dtype, shape, ntraj, dx, tol):
