@@ -12,13 +12,18 @@ namespace gpe {
 // small: a form with all three components in registers and every loop unrolled spent
 // most of its cycles waiting for instruction fetch at N = 4096 (255 registers, one block
 // per SM).  Stage twiddles and phases are read through L1.
-template <typename T, int N, int R, Sync SY>
+//
+// For short grids (N / R <= 64 threads per pencil) the block has G = 3 thread groups that
+// transform the three components at the same time (group g owns component g), so a lone
+// trajectory is not limited by the latency of three transforms in sequence; the local
+// step's site loop then runs over all 3 N / R threads.
+template <typename T, int N, int R, int G, Sync SY>
 __device__ __forceinline__ void kinetic_resident(cplx<T>* const (&buf)[3], const twel<T>* __restrict__ tws,
-                                                 const twel<T>* __restrict__ ph, int t) {
+                                                 const twel<T>* __restrict__ ph, int t, int grp) {
     using V = cplx<T>;
     constexpr int TP = N / R;
 #pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
+    for (int c = (G == 3 ? grp : 0); c < 3; c += G) {
         V v[1][R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[0][m] = buf[c][spad(t + m * TP)];
@@ -31,41 +36,52 @@ __device__ __forceinline__ void kinetic_resident(cplx<T>* const (&buf)[3], const
 #pragma unroll
         for (int m = 0; m < R; ++m) buf[c][spad(t + m * TP)] = v[0][m];
     }
-    pencil_sync<SY>();
+    __syncthreads();
 }
+
+// Component groups per block: 3 for short pencils (see kinetic_resident), else 1.
+template <typename T, int N>
+constexpr int res1d_groups() { return N / Tune<T>::kResR(N) <= 64 ? 3 : 1; }
+
+// Synchronisation inside one component's transform: a warp when the group is a whole warp
+// or the entire block fits in one, otherwise the block (all groups run the same stages).
+template <int TP, int G>
+constexpr Sync res1d_sync() { return (G == 1 ? TP <= 32 : (TP == 32 || G * TP <= 32)) ? Sync::Warp : Sync::Block; }
 
 // Blocks per SM the resident kernel is compiled for: as many as its shared memory allows
 // (at most 8), so that the register budget does not cap them further.
-template <typename T, int N>
+template <typename T, int N, int G>
 constexpr int res1d_blocks() {
     const int b = (227 * 1024) / (3 * smem_ld<T>(N) * (int)sizeof(cplx<T>) + 1024);
-    return b < 1 ? 1 : (b > 8 ? 8 : b);
+    const int cap = G == 3 ? 4 : 8;
+    return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
-template <typename T, int N, int R>
-__global__ void __launch_bounds__(N / R, res1d_blocks<T, N>())
+template <typename T, int N, int R, int G>
+__global__ void __launch_bounds__(G * (N / R), res1d_blocks<T, N, G>())
 k_resident1d(const Res1DArgs<T> a) {
     using V = cplx<T>;
     constexpr int TP = N / R;
+    constexpr int NT = G * TP;
     constexpr int LD = smem_ld<T>(N);
-    constexpr Sync SY = (TP <= 32) ? Sync::Warp : Sync::Block;
+    constexpr Sync SY = res1d_sync<TP, G>();
     extern __shared__ __align__(128) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
     const twel<T>* tws = a.tw[tw_slot<R>()];
-    const int t = threadIdx.x;
+    const int tid = threadIdx.x, grp = tid / TP, t = tid % TP;
     V* g = a.ptrs[blockIdx.x];
     V* const buf[3] = {sm, sm + LD, sm + 2 * LD};
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
-        for (int i = t; i < N; i += TP) buf[c][spad(i)] = g[c * N + i];
-    pencil_sync<SY>();
-    kinetic_resident<T, N, R, SY>(buf, tws, a.ph_half, t);
+        for (int i = tid; i < N; i += NT) buf[c][spad(i)] = g[c * N + i];
+    __syncthreads();
+    kinetic_resident<T, N, R, G, SY>(buf, tws, a.ph_half, t, grp);
     LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
         if (a.vpot == nullptr) {
 #pragma unroll 2
-            for (int i = t; i < N; i += TP) {
+            for (int i = tid; i < N; i += NT) {
                 const int k = spad(i);
                 V p1 = buf[0][k], p0 = buf[1][k], pm = buf[2][k];
                 local_step<T>(p1, p0, pm, coef);
@@ -75,7 +91,7 @@ k_resident1d(const Res1DArgs<T> a) {
             }
         } else {
 #pragma unroll 2
-            for (int i = t; i < N; i += TP) {
+            for (int i = tid; i < N; i += NT) {
                 const int k = spad(i);
                 V p1 = buf[0][k], p0 = buf[1][k], pm = buf[2][k];
                 local_step<true, T>(p1, p0, pm, coef, site_pot<T>(a.vpot, N, i));
@@ -84,19 +100,20 @@ k_resident1d(const Res1DArgs<T> a) {
                 buf[2][k] = pm;
             }
         }
-        pencil_sync<SY>();
-        kinetic_resident<T, N, R, SY>(buf, tws, (s == a.nsteps - 1) ? a.ph_half : a.ph_full, t);
+        __syncthreads();
+        kinetic_resident<T, N, R, G, SY>(buf, tws, (s == a.nsteps - 1) ? a.ph_half : a.ph_full, t, grp);
     }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
-        for (int i = t; i < N; i += TP) g[c * N + i] = buf[c][spad(i)];
+        for (int i = tid; i < N; i += NT) g[c * N + i] = buf[c][spad(i)];
 }
 
 template <typename T, int N>
 cudaError_t resident1d_n(const Res1DArgs<T>& a, cudaStream_t s) {
     constexpr int R = Tune<T>::kResR(N);
+    constexpr int G = res1d_groups<T, N>();
     const size_t smem = (size_t)3 * smem_ld<T>(N) * sizeof(cplx<T>);
-    return launch_with_smem(k_resident1d<T, N, R>, a.ntraj, N / R, smem, s, &a);
+    return launch_with_smem(k_resident1d<T, N, R, G>, a.ntraj, G * (N / R), smem, s, &a);
 }
 
 template <> int resident1d_max_n<float>() { return 4096; }
