@@ -171,6 +171,28 @@ def ncu_traffic(kernel_class):
 
 # ------------------------------------------------------------------ CPU oracle timing
 
+def cpu_model():
+    """Host CPU as /proc/cpuinfo names it (model name, or Arm implementer/part), and nproc."""
+    name = None
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        for key in ("model name", "Model"):
+            for line in info:
+                if line.lower().startswith(key.lower()):
+                    name = line.split(":", 1)[1].strip()
+                    break
+            if name:
+                break
+        if not name:
+            impl = next((l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")), None)
+            part = next((l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")), None)
+            if impl or part:
+                name = f"arm implementer {impl} part {part}"
+    except OSError:
+        pass
+    return {"model": name or "unknown", "nproc": os.cpu_count()}
+
+
 def oracle_sample(seconds_target=12.0):
     """Time the FP64 CPU oracle on a bounded sample of the workload: one 512^2 trajectory,
     as many Strang steps as fit in about ``seconds_target`` seconds, plus its spectra."""
@@ -191,6 +213,7 @@ def oracle_sample(seconds_target=12.0):
     el = time.perf_counter() - t0
     su = WL.sites * 3 * nsteps
     return {"value": su / el, "unit": "site-updates/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": f"1 trajectory of the 512^2 workload, {nsteps} steps + one spectra evaluation, "
                       f"{el:.1f} s, FP64 torch CPU"}
 
@@ -216,7 +239,7 @@ def run_reference(args):
            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WL.name, "grid": list(WL.shape), "ntraj": 1, "dt": WL.dt},
-           "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": torch.get_num_threads(),
+           "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": torch.get_num_threads(), "cpu": cpu_model(),
                             "kind": "oracle", "sample": samples[0] if samples else ""},
            "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
