@@ -31,7 +31,8 @@ def sample_steps(nsteps, nsamples, first):
 
 
 def run(n=4096, ntraj=304, dt=0.04, t_end=4.0e4, nsamples=20, t_first=200.0, c0n=1.0, c1n=-0.1, q=0.09,
-        density=1000.0, seed=20231005, dtype="c64", chunk=2500, kmax_ir=0.15, t_fit=2000.0):
+        density=1000.0, seed=20231005, dtype="c64", chunk=2500, kmax_ir=0.15, t_fit=2000.0,
+        uv_window=(0.3, 1.0), zeta_window=(0.05, 0.3)):
     c0, c1 = c0n / density, c1n / density
     nsteps = int(round(t_end / dt))
     steps = sample_steps(nsteps, nsamples, int(round(t_first / dt)))
@@ -85,6 +86,13 @@ def run(n=4096, ntraj=304, dt=0.04, t_end=4.0e4, nsamples=20, t_first=200.0, c0n
         a_c, b_c, r_c = scaling.collapse_exponents(tl, kbin, Sl, t_ref=t_ref, kmax=kmax_ir)
         res.update({"beta_moment": b_m, "alpha_moment": a_m, "beta_collapse": b_c, "alpha_collapse": a_c,
                     "collapse_residual": r_c, "t_ref": t_ref})
+        # UV window (the paper's second scaling region) and the power-law fall-off k^-zeta
+        a_u, b_u, r_u = scaling.collapse_exponents(tl, kbin, Sl, t_ref=t_ref, kmax=uv_window[1], kmin=uv_window[0],
+                                                   guess=(-0.1, -0.1))
+        zm = (kbin > zeta_window[0]) & (kbin < zeta_window[1])
+        zeta = -scaling.fit_power(kbin[zm], S[-1][zm])[0]
+        res.update({"uv_window": list(uv_window), "beta_uv": b_u, "alpha_uv": a_u, "uv_residual": r_u,
+                    "zeta_window": list(zeta_window), "zeta": zeta})
     return res, {"times": times, "k": kbin, "S_perp": S, "n_m": nm, "N": N, "Q_w": Q, "counts": counts}
 
 
