@@ -48,7 +48,8 @@ template <int N, int R> constexpr int rows_per_cta() { return (N / R) >= 256 ? 1
 constexpr uint32_t kWaitLimit = 1u << 22;   // mbarrier polls before a wait counts as expired
 
 // FFT along x of one row-component held in shared memory (thread t owns positions
-// t + m TP), times a phase table, inverse FFT, back into shared memory.
+// t + m TP), times a phase table, inverse FFT, back into shared memory.  A row of at most
+// 32 threads lies within one warp, so its exchanges synchronise the warp only.
 template <typename T, int N, int R>
 __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const twel<T>* tws,
                                             const twel<T>* __restrict__ ph, int t) {
@@ -58,10 +59,11 @@ __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const t
     V* const xb[1] = {xbuf};
 #pragma unroll
     for (int m = 0; m < R; ++m) v[0][m] = row[t + m * TP];
-    fft_pencil<N, R, -1, 1, Sync::Block>(v, xb, tws, t);
+    constexpr Sync SY = TP <= 32 ? Sync::Warp : Sync::Block;
+    fft_pencil<N, R, -1, 1, SY>(v, xb, tws, t);
 #pragma unroll
     for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
-    fft_pencil<N, R, +1, 1, Sync::Block>(v, xb, tws, t);
+    fft_pencil<N, R, +1, 1, SY>(v, xb, tws, t);
 #pragma unroll
     for (int m = 0; m < R; ++m) row[t + m * TP] = v[0][m];
 }
