@@ -15,7 +15,7 @@ namespace gpe {
 template <typename T> struct Tune;
 template <> struct Tune<float> {
     static constexpr int kXR = 8;        // points per thread, row pass (3 components live)
-    static constexpr int kColR(int n) { return n >= 1024 ? 16 : 8; }   // points per thread, column pass
+    static constexpr int kColR(int n) { return n >= 128 ? 16 : 8; }    // points per thread, column pass
     static constexpr int kColCols(int n) { return n >= 1024 ? 4 : (n >= 512 ? 4 : (n >= 256 ? 8 : 16)); }
     static constexpr int kResR(int n) { return n >= 1024 ? 16 : 8; }
     static constexpr int kRowR(int n) { return n >= 256 ? 16 : 8; }
