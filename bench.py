@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", choices=["2d", "1d", "3d", "ragged", "adjoint", "paper1d", "paper1d_f64"], default="2d",
                    help="2d: the benchmark workload (default); others print a line for that configuration")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="fixed default column-pass tile widths (for launch lists under ncu, whose timing "
+                        "would mislead the tuner)")
     p.add_argument("--ncu-case", action="store_true",
                    help="small profiling target: the 512^2 x 64 batch (403 MB > L2), 4 steps + observables")
     return p.parse_args()
@@ -256,6 +259,8 @@ def run_ours(args):
     seed = W.SEED_BASE
     b = B.GPEBatch(WL.shape, WL.ntraj, "c64", WL.c0, WL.c1, WL.q, WL.dt, dx=WL.dx)
     b.set_traj_base(sharding.trajectory_base(rank, WL.ntraj))
+    if args.no_autotune:
+        b.set_autotune(False)
     nb, sd = b.layout()
     nslots = args.warmup + args.steps
     acc = torch.zeros(nslots * sd, dtype=torch.float64, device=dev)
