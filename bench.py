@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true",
                    help="fixed default column-pass tile widths (for launch lists under ncu, whose timing "
                         "would mislead the tuner)")
+    p.add_argument("--alu-peaks", action="store_true",
+                   help="measure the FP32 / packed FP32 / FP64 FMA rates (roofline of the compute-bound passes)")
     p.add_argument("--ncu-case", action="store_true",
                    help="small profiling target: the 512^2 x 64 batch (403 MB > L2), 4 steps + observables")
     return p.parse_args()
@@ -503,9 +505,27 @@ def run_adjoint(args):
                       "config": {"workload": wl.name, "knots": 64, "checkpoint_every": 256}}), flush=True)
 
 
+def alu_peaks():
+    """FMA throughput (best of 3 launches per kind) with the SM clocks seen meanwhile."""
+    import torch
+    from paper_2310_03636_gb300 import binding as B
+    torch.cuda.init()
+    kinds = {"fp32_fma": (0, 1 << 16), "fp32x2_fma": (1, 1 << 15), "fp64_fma": (2, 1 << 10)}
+    out = {}
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    for name, (kind, iters) in kinds.items():
+        out[name + "_tflops"] = max(B.gpe_fma_rate(kind, iters) for _ in range(3)) / 1e12
+    out["clocks"] = clk.stop()
+    print(json.dumps({"alu_peaks": out, "sms": torch.cuda.get_device_properties(0).multi_processor_count}),
+          flush=True)
+
+
 def main():
     args = parse()
-    if args.ncu_case:
+    if args.alu_peaks:
+        alu_peaks()
+    elif args.ncu_case:
         ncu_case()
     elif args.workload != "2d":
         run_other(args)

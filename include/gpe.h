@@ -251,6 +251,15 @@ gpe_status gpe_diagnostics_noalloc(const void* psi, int32_t ntraj, int32_t ndim,
  * its sin and cos, then CUDA's sincosf of the same x.  Errors: GPE_EINVAL (NULL, n < 0). */
 gpe_status gpe_check_sincos(const float* x, float* out, int64_t n, void* stream);
 
+/* Arithmetic-rate probe (measurement support for the roofline of the compute-bound
+ * passes; not part of the method): times one launch that fills every SM with independent
+ * FMA chains and writes the rate to *flops_per_s (host), counting an FMA as 2 flops.
+ * kind 0: FP32 fma, 1: FP32 through the packed two-lane fma, 2: FP64 fma.  iters sets
+ * the work per thread (256 flops per trip; about 2^16 for FP32, 2^10 for FP64 gives a
+ * launch of tens of ms).  Synchronises the stream.  Errors: GPE_EINVAL (NULL, iters <= 0,
+ * unknown kind), GPE_ECUDA. */
+gpe_status gpe_fma_rate(int32_t kind, int64_t iters, double* flops_per_s, void* stream);
+
 /* Number of kernels this library has launched since it was loaded (all batches). */
 int64_t gpe_launch_count(void);
 

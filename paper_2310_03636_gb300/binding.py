@@ -69,6 +69,7 @@ def _load():
         "gpe_batch_get_tiles": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
         "gpe_batch_set_mean_field": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
+        "gpe_fma_rate": ([i32, i64, ctypes.POINTER(dbl), vp], ctypes.c_int),
         "gpe_diagnostics_noalloc": ([vp, i32, i32, ctypes.POINTER(i32), dbl, ctypes.c_int, dbl, dbl, dbl, vp, vp],
                                     ctypes.c_int),
         "gpe_last_error": ([], ctypes.c_char_p),
@@ -230,6 +231,14 @@ def gpe_check_sincos(x, stream=None):
     _check(LIB.gpe_check_sincos(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
                                 _stream(stream)))
     return out
+
+
+def gpe_fma_rate(kind, iters, stream=None):
+    """FMA throughput of the current device in flop/s (kind 0: FP32, 1: packed FP32 pairs,
+    2: FP64); one timed launch of ``iters`` loop trips per thread."""
+    out = ctypes.c_double(0.0)
+    _check(LIB.gpe_fma_rate(int(kind), int(iters), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 # ----------------------------------------------------------------- convenience

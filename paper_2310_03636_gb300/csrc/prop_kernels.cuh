@@ -231,25 +231,35 @@ struct ColTmaArgs {
     int* status;
 };
 
+// Elements of one tile buffer: the tile ([N][COLS], as the TMA engine writes it) and,
+// once every thread holds its points, the COLS padded exchange pencils of the transform,
+// rounded to whole 128-byte lines so the second buffer is as aligned as the first.
 template <typename T, int N, int COLS>
-constexpr size_t colpass_tma_smem(int R) {
-    return (size_t)2 * N * COLS * sizeof(cplx<T>) + (size_t)tw_off<T>(COLS * smem_ld_cols<T>(N, COLS)) * sizeof(cplx<T>);
+constexpr int colpass_tma_buf() {
+    constexpr int E = N * COLS > COLS * smem_ld_cols<T>(N, COLS) ? N * COLS : COLS * smem_ld_cols<T>(N, COLS);
+    constexpr int L = 128 / (int)sizeof(cplx<T>);
+    return (E + L - 1) / L * L;
+}
+
+template <typename T, int N, int COLS>
+constexpr size_t colpass_tma_smem() {
+    return (size_t)2 * colpass_tma_buf<T, N, COLS>() * sizeof(cplx<T>);
 }
 
 template <typename T, int N, int R, int COLS, bool FWD_ONLY, bool ZPASS>
-__global__ void __launch_bounds__(COLS * (N / R))
+__global__ void __launch_bounds__(COLS * (N / R), (COLS * (N / R)) < 512 ? 512 / (COLS * (N / R)) : 1)
 k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
     using V = cplx<T>;
     constexpr int TP = N / R;
     constexpr int LD = smem_ld_cols<T>(N, COLS);
+    constexpr int SB = colpass_tma_buf<T, N, COLS>();
     constexpr int TWN = FftPlan<N, R>::tw_size();
     constexpr int BOX = N < 256 ? N : 256;
     constexpr int NBOX = N / BOX;
     constexpr uint32_t TILE_BYTES = (uint32_t)(N * COLS * sizeof(V));
     extern __shared__ __align__(128) unsigned char smraw[];
-    V* buf = reinterpret_cast<V*>(smraw);                                   // [2][N][COLS]
-    V* X = buf + 2 * N * COLS;                                              // [COLS][LD]
-    twel<T>* tws = reinterpret_cast<twel<T>*>(X + tw_off<T>(COLS * LD));
+    V* buf = reinterpret_cast<V*>(smraw);                                   // [2][SB]
+    twel<T>* tws = reinterpret_cast<twel<T>*>(buf + 2 * SB);
     uint64_t* bar = reinterpret_cast<uint64_t*>(tws + TWN);
     const int col = threadIdx.x % COLS, t = threadIdx.x / COLS;
     const void* map = &tmap;
@@ -269,7 +279,7 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
     auto issue_load = [&](int tile, int st) {
         int c0, c1, c2;
         coords(tile, c0, c1, c2);
-        V* dst = buf + st * N * COLS;
+        V* dst = buf + st * SB;
         mbar_expect_tx(&bar[st], TILE_BYTES);
 #pragma unroll
         for (int b = 0; b < NBOX; ++b) {
@@ -280,7 +290,7 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
     auto issue_store = [&](int tile, int st) {
         int c0, c1, c2;
         coords(tile, c0, c1, c2);
-        const V* src = buf + st * N * COLS;
+        const V* src = buf + st * SB;
 #pragma unroll
         for (int b = 0; b < NBOX; ++b) {
             if constexpr (ZPASS) tma_store_3d(map, c0, c1, c2 + b * BOX, src + b * BOX * COLS);
@@ -300,17 +310,21 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
     }
     copy_table(tws, a.tw, TWN);
     __syncthreads();
-    V* const xb[1] = {X + col * LD};
     int it = 0;
     bool ok = true;
     for (int tile = first; tile < a.n_tiles; tile += stride, ++it) {
         const int st = it & 1;
-        V* bs = buf + st * N * COLS;
+        V* bs = buf + st * SB;
         ok = __syncthreads_and(mbar_wait(&bar[st], (uint32_t)((it >> 1) & 1), kWaitLimit));
         if (!ok) break;
         V v[1][R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[0][m] = bs[(t + m * TP) * COLS + col];
+        // The transform exchanges through the same buffer (column col at bs + col LD): every
+        // thread must hold its points first.  Each exchange ends with a barrier after its
+        // reads, so the results can be written back in tile order right after the transform.
+        __syncthreads();
+        V* const xb[1] = {bs + col * LD};
         fft_pencil<N, R, -1, 1, Sync::Block>(v, xb, tws, t);
         if constexpr (!FWD_ONLY) {
 #pragma unroll
@@ -408,14 +422,15 @@ cudaError_t colpass_n(const PassArgs<T>& a, cudaStream_t s) {
 
 // The persistent column pass is launched with as many blocks as can be resident at once
 // (occupancy query, once per kernel): every SM holds the same number of blocks, each walks
-// the tiles with the grid stride.  At 512 (FP32) that is 3 blocks per SM with 80 registers
-// a thread; a 4th does not fit the shared memory.  More blocks than fit would run as a
-// second, partial wave.
+// the tiles with the grid stride.  The launch bounds cap a thread at 128 registers (512
+// threads per SM); at 512 (FP32, 4 columns) that is 4 blocks per SM with 42 KB of shared
+// memory each (3 while the exchange had a buffer of its own).  More blocks than fit would
+// run as a second, partial wave.
 template <typename T, int N, int COLS, bool FWD_ONLY, bool ZPASS>
 cudaError_t colpass_tma_n(const CUtensorMap& map, const ColTmaArgs<T>& a, int sms, cudaStream_t s) {
     constexpr int R = Tune<T>::kColR(N);
     constexpr int THREADS = COLS * (N / R);
-    const size_t smem = colpass_tma_smem<T, N, COLS>(R) + FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
+    const size_t smem = colpass_tma_smem<T, N, COLS>() + FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
     auto kern = k_colpass_tma<T, N, R, COLS, FWD_ONLY, ZPASS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -52,3 +52,8 @@ def test_argument_errors_without_gpu(lib):
     assert lib.gpe_last_error()
     lib.gpe_step_batch.restype = ctypes.c_int
     assert lib.gpe_step_batch(None, ctypes.c_int64(1), None) == 1
+    lib.gpe_fma_rate.restype = ctypes.c_int
+    rate = ctypes.c_double(0.0)
+    assert lib.gpe_fma_rate(ctypes.c_int32(3), ctypes.c_int64(16), ctypes.byref(rate), None) == 1
+    assert lib.gpe_fma_rate(ctypes.c_int32(0), ctypes.c_int64(0), ctypes.byref(rate), None) == 1
+    assert lib.gpe_fma_rate(ctypes.c_int32(0), ctypes.c_int64(16), None, None) == 1

@@ -323,6 +323,18 @@ def test_own_sincos_against_cuda(B):
     assert (out[:, 1] - c_ref).abs().max() <= (out[:, 3] - c_ref).abs().max() + 1.5e-7
 
 
+def test_fma_rate_probe(B):
+    """The arithmetic-rate probe returns finite, ordered rates: FP32 above FP64, and below
+    what 152 SMs x 128 lanes x 2 flops at 2.1 GHz x 2 (packed) could give."""
+    r32 = B.gpe_fma_rate(0, 1 << 12)
+    r64 = B.gpe_fma_rate(2, 1 << 8)
+    r2 = B.gpe_fma_rate(1, 1 << 11)
+    ceiling = 152 * 128 * 2 * 2.1e9 * 2
+    for r in (r32, r64, r2):
+        assert np.isfinite(r) and 0 < r < ceiling
+    assert r32 > r64
+
+
 @pytest.mark.parametrize("dtype,n,steps,tol", [("c128", 4096, 120, 1e-11), ("c128", 8192, 60, 1e-11),
                                                ("c128", 16384, 40, 1e-11), ("c64", 8192, 200, 1e-4),
                                                ("c64", 16384, 200, 1e-4), ("c64", 32768, 200, 1e-4)])
