@@ -189,6 +189,15 @@ gpe_status gpe_batch_set_graph(gpe_batch* batch, int32_t enable);
  * for FP64 and non-contiguous groups, fixed per-size defaults are used. */
 gpe_status gpe_batch_set_autotune(gpe_batch* batch, int32_t enable);
 
+/* Fixes the tile widths of the strided passes for trajectory traj's group (and so for
+ * every trajectory of its shape group): cols_y for y, cols_z for z, 0 keeps the current
+ * width.  Each must be a width the pass is built for at that size (2, 4, 8 from n = 256,
+ * 4, 8, 16 below) and divide nx; the autotuner then leaves the group alone.  The width
+ * changes no result bit.  Errors: GPE_EINVAL (bad batch, trajectory or width),
+ * GPE_EUNSUPPORTED (FP64 batches, 1D groups, groups whose fields are not back to back),
+ * GPE_ECUDA. */
+gpe_status gpe_batch_set_tiles(gpe_batch* batch, int32_t traj, int32_t cols_y, int32_t cols_z);
+
 /* Tile widths in use for trajectory traj's group: cols[0] for y, cols[1] for z (0 where the
  * group has no such pass or uses the non-tensor-map pass), *tuned = 1 once the autotuner
  * has run for the group (tuned may be NULL).  Errors: GPE_EINVAL. */

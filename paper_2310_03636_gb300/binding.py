@@ -67,6 +67,7 @@ def _load():
         "gpe_batch_set_potential": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
         "gpe_batch_set_autotune": ([vp, i32], ctypes.c_int),
         "gpe_batch_get_tiles": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+        "gpe_batch_set_tiles": ([vp, i32, i32, i32], ctypes.c_int),
         "gpe_batch_set_mean_field": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_fma_rate": ([i32, i64, ctypes.POINTER(dbl), vp], ctypes.c_int),
@@ -333,6 +334,10 @@ class GPEBatch:
 
     def set_autotune(self, enable=True):
         _check(LIB.gpe_batch_set_autotune(self.h, 1 if enable else 0))
+
+    def set_tiles(self, cols_y, cols_z=0, traj=0):
+        """Fix the strided passes' tile widths of trajectory traj's shape group (0 keeps one)."""
+        _check(LIB.gpe_batch_set_tiles(self.h, int(traj), int(cols_y), int(cols_z)))
 
     def tiles(self, traj=0):
         """(cols_y, cols_z, tuned) of the column passes of trajectory traj's group."""

@@ -440,7 +440,7 @@ gpe_status tune_tiles(gpe_batch* b, cudaStream_t s) {
     }
     if (cs != cudaStreamCaptureStatusNone) return GPE_OK;
     for (Group& g : b->groups) {
-        if (g.tuned || !g.contiguous || g.ndim < 2) continue;
+        if (g.tuned || g.fixed || !g.contiguous || g.ndim < 2) continue;
         g.tuned = true;
         const size_t per_traj = (size_t)3 * g.sites * sizeof(float2);
         const size_t cap = ((size_t)256 << 20) / per_traj;
@@ -1011,6 +1011,36 @@ gpe_status gpe_batch_set_mean_field(gpe_batch* b, const int32_t n[3], const doub
 gpe_status gpe_batch_set_autotune(gpe_batch* b, int32_t enable) {
     if (!b) return fail(GPE_EINVAL, "batch is NULL");
     b->autotune = enable != 0;
+    return GPE_OK;
+}
+
+gpe_status gpe_batch_set_tiles(gpe_batch* b, int32_t traj, int32_t cols_y, int32_t cols_z) {
+    g_err.clear();
+    if (!b || traj < 0 || traj >= (int32_t)b->trajs.size()) return fail(GPE_EINVAL, "bad batch or trajectory");
+    Group* gp = nullptr;
+    for (Group& g : b->groups)
+        for (int id : g.ids)
+            if (id == traj) gp = &g;
+    if (!gp) return fail(GPE_EINVAL, "trajectory %d not found", traj);
+    Group& g = *gp;
+    if (b->dtype != GPE_C64 || !g.contiguous || g.ndim < 2)
+        return fail(GPE_EUNSUPPORTED, "tile widths are selectable for FP32 2D/3D groups with back-to-back fields");
+    if (cols_y < 0 || cols_z < 0 || (g.ndim < 3 && cols_z != 0)) return fail(GPE_EINVAL, "bad tile widths");
+    const int want[3] = {0, cols_y, cols_z};
+    for (int ax = 1; ax < g.ndim; ++ax) {
+        if (want[ax] == 0) continue;
+        int cand[8];
+        const int nc = colpass_tma_candidates<float>(g.n[ax], cand);
+        bool built = false;
+        for (int i = 0; i < nc; ++i) built = built || cand[i] == want[ax];
+        if (!built || g.n[0] % want[ax])
+            return fail(GPE_EINVAL, "tile width %d is not built for n = %d (nx = %d)", want[ax], g.n[ax], g.n[0]);
+    }
+    for (int ax = 1; ax < g.ndim; ++ax)
+        if (want[ax]) g.cols[ax] = want[ax];
+    g.fixed = true;
+    if (!encode_group_maps(g, 4)) return fail(GPE_ECUDA, "tensor maps for the new tile widths");
+    drop_graphs(b);
     return GPE_OK;
 }
 

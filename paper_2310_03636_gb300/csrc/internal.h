@@ -87,6 +87,7 @@ struct Group {
     CUtensorMap map_z{};           // 3D map {2 nx, ny, nz 3 ntraj} (ndim == 3)
     int cols[3] = {0, 0, 0};       // column-pass tile width per axis (1: y, 2: z)
     bool tuned = false;            // tile widths chosen by timing
+    bool fixed = false;            // tile widths set by the caller (the autotuner skips the group)
     const void* vpot = nullptr;    // caller's potential [3][sites] (real, the batch's precision), or null
     const double* mean_field = nullptr;   // caller's initial mean field [3][sites] complex FP64, or null
 };

@@ -57,3 +57,5 @@ def test_argument_errors_without_gpu(lib):
     assert lib.gpe_fma_rate(ctypes.c_int32(3), ctypes.c_int64(16), ctypes.byref(rate), None) == 1
     assert lib.gpe_fma_rate(ctypes.c_int32(0), ctypes.c_int64(0), ctypes.byref(rate), None) == 1
     assert lib.gpe_fma_rate(ctypes.c_int32(0), ctypes.c_int64(16), None, None) == 1
+    lib.gpe_batch_set_tiles.restype = ctypes.c_int
+    assert lib.gpe_batch_set_tiles(None, 0, 4, 0) == 1

@@ -434,6 +434,37 @@ def test_full_size_3d_256_sampled(B):
     assert np.abs(d1[:, :3].sum(1) - N0).max() < 1e-5 * N0.max()
     b.close()
 
+@pytest.mark.parametrize("shape,ntraj", [((256, 256), 3), ((64, 64, 64), 2), ((256, 64, 128), 2)])
+def test_every_tile_width_gives_the_same_bits(B, shape, ntraj):
+    """Every built tile width of the strided passes, fixed through gpe_batch_set_tiles, gives
+    the fields of the default widths bit for bit; widths that are not built are refused."""
+    def cands(n):
+        return (2, 4, 8) if n >= 256 else (4, 8, 16)
+    ny = shape[-2]   # shapes are (z,) y, x
+    combos = [(cy, 0) for cy in cands(ny)] if len(shape) == 2 else \
+        [(cy, cz) for cy in cands(ny) for cz in cands(shape[-3])]
+    out = {}
+    for cy, cz in [(None, None)] + combos:
+        b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, 0.02)
+        b.set_autotune(False)
+        if cy is not None:
+            b.set_tiles(cy, cz)
+            assert b.tiles(0)[:2] == (cy, cz)
+        b.init_noise(5, MEAN, 0.5)
+        b.step(6)
+        assert b.sync_status() == B.GPE_OK
+        out[(cy, cz)] = b.psi.cpu().numpy()
+        if cy is None:
+            with pytest.raises(B.GPEError):
+                b.set_tiles(3)
+            with pytest.raises(B.GPEError):
+                b.set_tiles(cands(ny)[0], 4 if len(shape) == 2 else 32)
+        b.close()
+    ref = out.pop((None, None))
+    for key, v in out.items():
+        np.testing.assert_array_equal(v, ref, err_msg=f"tile widths {key}")
+
+
 
 @pytest.mark.parametrize("shape,ntraj", [((256, 256), 4), ((64, 128, 64), 2), ((128, 1024), 2)])
 def test_autotuned_tiles_change_no_bit(B, shape, ntraj):
