@@ -315,28 +315,56 @@ def run_ours(args):
                 "classes_launches": {k: v[1] for k, v in prof.items() if v[1]},
                 "effective_frac_16B_per_su": value / ws * 16.0 / (peak * 1e9)}
 
-    # end to end through the API with host buffers: H2D of the initial fields from pinned
-    # memory, the sampling interval, D2H of the accumulator slot
+    # end to end through the API with host buffers: every bench step copies its initial
+    # fields from pinned host memory, runs the sampling interval and reads its accumulator
+    # slot back.  Two field buffers (two batches of the same ensemble): the copy for step
+    # k + 1 runs on a copy stream while step k computes, the way a pipelined caller would.
     host_psi = torch.empty_like(b.psi, device="cpu").pin_memory()
     host_psi.copy_(b.psi)
     host_acc = torch.empty(sd, dtype=torch.float64).pin_memory()
+    b2 = B.GPEBatch(WL.shape, WL.ntraj, "c64", WL.c0, WL.c1, WL.q, WL.dt, dx=WL.dx)
+    b2.set_traj_base(sharding.trajectory_base(rank, WL.ntraj))
+    if args.no_autotune:
+        b2.set_autotune(False)
+    b2.psi.copy_(host_psi)
+    b2.step(STEPS_PER_SAMPLE)   # first step: tile tuning
+    bufs = (b, b2)
+    cstream = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in bufs]
+    freed = [torch.cuda.Event() for _ in bufs]
+
+    def put(k):
+        i = k % 2
+        cstream.wait_event(freed[i])   # the buffer's previous step has finished with it
+        with torch.cuda.stream(cstream):
+            bufs[i].psi.copy_(host_psi, non_blocking=True)
+        copied[i].record(cstream)
+
     k_e2e = max(3, args.steps // 2)
     torch.cuda.synchronize()
     barrier(ws)
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
     f0.record(stream)
+    cstream.wait_event(f0)
+    put(0)
     for k in range(k_e2e):
-        b.psi.copy_(host_psi, non_blocking=True)
-        b.step(STEPS_PER_SAMPLE)
-        b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 0)
+        i = k % 2
+        if k + 1 < k_e2e:
+            put(k + 1)
+        stream.wait_event(copied[i])
+        bufs[i].step(STEPS_PER_SAMPLE)
+        bufs[i].observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 0)
         host_acc.copy_(acc[:sd], non_blocking=True)
+        freed[i].record(stream)
     f1.record(stream)
     torch.cuda.synchronize()
+    assert b2.sync_status() == B.GPE_OK
+    b2.close()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1), ws)
     e2e = {"value": su_per_step * k_e2e * ws / (e2e_ms * 1e-3), "unit": "site-updates/s",
            "h2d_bytes_per_step": int(b.psi.numel() * b.psi.element_size()),
-           "d2h_bytes_per_step": int(sd * 8), "steps": k_e2e}
+           "d2h_bytes_per_step": int(sd * 8), "steps": k_e2e,
+           "pipelined": "two field buffers; the next step's H2D copy overlaps the current step"}
     tiles = b.tiles(0)
     b.close()
 
