@@ -223,6 +223,15 @@ def oracle_sample(seconds_target=12.0):
                       f"{el:.1f} s, FP64 torch CPU"}
 
 
+def workload_config(ws):
+    """The bench workload as both arms name it in their JSON line."""
+    return {"workload": WL.name, "grid": list(WL.shape), "ntraj_per_gpu": WL.ntraj,
+            "dt": WL.dt, "steps_per_bench_step": STEPS_PER_SAMPLE,
+            "observables_every": STEPS_PER_SAMPLE, "c0": WL.c0, "c1": WL.c1, "q": WL.q,
+            "parallelism": f"trajectories sharded over {ws} GPU(s)",
+            "l2": "inputs larger than L2 (403 MB of fields per GPU)"}
+
+
 def run_reference(args):
     ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
@@ -243,7 +252,7 @@ def run_reference(args):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WL.name, "grid": list(WL.shape), "ntraj": 1, "dt": WL.dt},
+           "config": workload_config(ws),
            "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": torch.get_num_threads(), "cpu": cpu_model(),
                             "kind": "oracle", "sample": samples[0] if samples else ""},
            "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -396,12 +405,7 @@ def run_ours(args):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": {"workload": WL.name, "grid": list(WL.shape), "ntraj_per_gpu": WL.ntraj,
-                          "dt": WL.dt, "steps_per_bench_step": STEPS_PER_SAMPLE,
-                          "observables_every": STEPS_PER_SAMPLE, "c0": WL.c0, "c1": WL.c1, "q": WL.q,
-                          "parallelism": f"trajectories sharded over {ws} GPU(s)",
-                          "l2": "inputs larger than L2 (403 MB of fields per GPU)",
-                          "column_tiles": {"y": tiles[0], "autotuned": tiles[2]}},
+               "config": dict(workload_config(ws), column_tiles={"y": tiles[0], "autotuned": tiles[2]}),
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": launches, "fp64_plain": fp64, "status": status}
         print(json.dumps(out), flush=True)
