@@ -153,10 +153,13 @@ struct FftPlan {
     static constexpr int tw_size() { return tw_offset(kStages); }
 };
 
-// One Stockham stage S of radix RS on sub-transforms of length NS.
-template <int N, int R, int DIR, int NC, int S, Sync SY, typename V, typename TW>
+// One Stockham stage S of radix RS on sub-transforms of length NS.  With SPLIT > 0 the
+// twiddles of the stages whose entries start at or after SPLIT come from tws_hi (the
+// table's tail, e.g. left in global memory) and the others from tws.
+template <int N, int R, int DIR, int NC, int S, Sync SY, int SPLIT = 0, typename V, typename TW>
 __device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC],
-                                               const TW* __restrict__ tws, int t) {
+                                               const TW* __restrict__ tws, int t,
+                                               const TW* __restrict__ tws_hi = nullptr) {
     using P = FftPlan<N, R>;
     constexpr int TP = N / R;
     constexpr int RS = P::radix(S);
@@ -176,7 +179,9 @@ __device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC
         if constexpr (NS > 1) {
 #pragma unroll
             for (int r = 1; r < RS; ++r) {
-                const TW f = tws[OFF + (r - 1) * NS + k];
+                TW f;
+                if constexpr (SPLIT > 0 && OFF >= SPLIT) f = tws_hi[OFF + (r - 1) * NS + k];
+                else f = tws[OFF + (r - 1) * NS + k];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) w[c][r] = twmul<DIR>(w[c][r], f);
             }
@@ -206,12 +211,13 @@ __device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC
     }
 }
 
-template <int N, int R, int DIR, int NC, int S, Sync SY, typename V, typename TW>
+template <int N, int R, int DIR, int NC, int S, Sync SY, int SPLIT = 0, typename V, typename TW>
 __device__ __forceinline__ void stockham_from(V (&v)[NC][R], V* const (&buf)[NC],
-                                              const TW* __restrict__ tws, int t) {
+                                              const TW* __restrict__ tws, int t,
+                                              const TW* __restrict__ tws_hi = nullptr) {
     if constexpr (S < FftPlan<N, R>::kStages) {
-        stockham_stage<N, R, DIR, NC, S, SY>(v, buf, tws, t);
-        stockham_from<N, R, DIR, NC, S + 1, SY>(v, buf, tws, t);
+        stockham_stage<N, R, DIR, NC, S, SY, SPLIT>(v, buf, tws, t, tws_hi);
+        stockham_from<N, R, DIR, NC, S + 1, SY, SPLIT>(v, buf, tws, t, tws_hi);
     }
 }
 
@@ -224,6 +230,16 @@ __device__ __forceinline__ void fft_pencil(V (&v)[NC][R], V* const (&buf)[NC],
                                            const TW* __restrict__ tws, int t) {
     static_assert((N & (N - 1)) == 0 && N >= R, "N must be a power of two >= R");
     stockham_from<N, R, DIR, NC, 0, SY>(v, buf, tws, t);
+}
+
+// The same transform with the stage-twiddle table in two parts: entries [0, SPLIT) from
+// tws_lo (a shared-memory copy of the table's head) and the rest from tws_hi (the full
+// table, typically in global memory).  SPLIT must be a stage boundary of FftPlan<N, R>.
+template <int N, int R, int DIR, int NC, Sync SY, int SPLIT, typename V, typename TW>
+__device__ __forceinline__ void fft_pencil_split(V (&v)[NC][R], V* const (&buf)[NC], const TW* __restrict__ tws_lo,
+                                                 const TW* __restrict__ tws_hi, int t) {
+    static_assert((N & (N - 1)) == 0 && N >= R, "N must be a power of two >= R");
+    stockham_from<N, R, DIR, NC, 0, SY, SPLIT>(v, buf, tws_lo, t, tws_hi);
 }
 
 // Cooperative copy of a table into shared memory (caller synchronises).

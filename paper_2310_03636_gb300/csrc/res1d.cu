@@ -17,9 +17,21 @@ namespace gpe {
 // transform the three components at the same time (group g owns component g), so a lone
 // trajectory is not limited by the latency of three transforms in sequence; the local
 // step's site loop then runs over all 3 N / R threads.
+//
+// The stage twiddles of the first twiddled stage (R - 1 rows of R entries: 3.8 KB at
+// R = 16) sit in shared memory beside the field, tws_s; the later stages' entries, and the
+// phases, are read through L1 (tws).
+template <typename T, int N, int R>
+constexpr int res1d_tw_split() {
+    using P = FftPlan<N, R>;
+    return P::kStages > 2 ? P::tw_offset(2) : P::tw_size();
+}
+
 template <typename T, int N, int R, int G, Sync SY>
-__device__ __forceinline__ void kinetic_resident(cplx<T>* const (&buf)[3], const twel<T>* __restrict__ tws,
-                                                 const twel<T>* __restrict__ ph, int t, int grp) {
+__device__ __forceinline__ void kinetic_resident(cplx<T>* const (&buf)[3], const twel<T>* tws_s,
+                                                 const twel<T>* __restrict__ tws, const twel<T>* __restrict__ ph,
+                                                 int t, int grp) {
+    constexpr int SPLIT = res1d_tw_split<T, N, R>();
     using V = cplx<T>;
     constexpr int TP = N / R;
 #pragma unroll 1
@@ -29,10 +41,10 @@ __device__ __forceinline__ void kinetic_resident(cplx<T>* const (&buf)[3], const
         for (int m = 0; m < R; ++m) v[0][m] = buf[c][spad(t + m * TP)];
         pencil_sync<SY>();   // every thread has its points before the first exchange overwrites
         V* const b1[1] = {buf[c]};
-        fft_pencil<N, R, -1, 1, SY>(v, b1, tws, t);
+        fft_pencil_split<N, R, -1, 1, SY, SPLIT>(v, b1, tws_s, tws, t);
 #pragma unroll
         for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
-        fft_pencil<N, R, +1, 1, SY>(v, b1, tws, t);
+        fft_pencil_split<N, R, +1, 1, SY, SPLIT>(v, b1, tws_s, tws, t);
 #pragma unroll
         for (int m = 0; m < R; ++m) buf[c][spad(t + m * TP)] = v[0][m];
     }
@@ -50,9 +62,14 @@ constexpr Sync res1d_sync() { return (G == 1 ? TP <= 32 : (TP == 32 || G * TP <=
 
 // Blocks per SM the resident kernel is compiled for: as many as its shared memory allows
 // (at most 8), so that the register budget does not cap them further.
+template <typename T, int N, int R>
+constexpr size_t res1d_smem() {
+    return (size_t)tw_off<T>(3 * smem_ld<T>(N)) * sizeof(cplx<T>) + (size_t)res1d_tw_split<T, N, R>() * sizeof(twel<T>);
+}
+
 template <typename T, int N, int G>
 constexpr int res1d_blocks() {
-    const int b = (227 * 1024) / (3 * smem_ld<T>(N) * (int)sizeof(cplx<T>) + 1024);
+    const int b = (227 * 1024) / ((int)res1d_smem<T, N, Tune<T>::kResR(N)>() + 1024);
     const int cap = G == 3 ? 4 : 8;
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
@@ -68,14 +85,16 @@ k_resident1d(const Res1DArgs<T> a) {
     extern __shared__ __align__(128) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
     const twel<T>* tws = a.tw[tw_slot<R>()];
+    twel<T>* tws_s = reinterpret_cast<twel<T>*>(sm + tw_off<T>(3 * LD));
     const int tid = threadIdx.x, grp = tid / TP, t = tid % TP;
     V* g = a.ptrs[blockIdx.x];
     V* const buf[3] = {sm, sm + LD, sm + 2 * LD};
+    copy_table(tws_s, tws, res1d_tw_split<T, N, R>());
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
         for (int i = tid; i < N; i += NT) buf[c][spad(i)] = g[c * N + i];
     __syncthreads();
-    kinetic_resident<T, N, R, G, SY>(buf, tws, a.ph_half, t, grp);
+    kinetic_resident<T, N, R, G, SY>(buf, tws_s, tws, a.ph_half, t, grp);
     LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
@@ -101,7 +120,7 @@ k_resident1d(const Res1DArgs<T> a) {
             }
         }
         __syncthreads();
-        kinetic_resident<T, N, R, G, SY>(buf, tws, (s == a.nsteps - 1) ? a.ph_half : a.ph_full, t, grp);
+        kinetic_resident<T, N, R, G, SY>(buf, tws_s, tws, (s == a.nsteps - 1) ? a.ph_half : a.ph_full, t, grp);
     }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
@@ -112,8 +131,7 @@ template <typename T, int N>
 cudaError_t resident1d_n(const Res1DArgs<T>& a, cudaStream_t s) {
     constexpr int R = Tune<T>::kResR(N);
     constexpr int G = res1d_groups<T, N>();
-    const size_t smem = (size_t)3 * smem_ld<T>(N) * sizeof(cplx<T>);
-    return launch_with_smem(k_resident1d<T, N, R, G>, a.ntraj, G * (N / R), smem, s, &a);
+    return launch_with_smem(k_resident1d<T, N, R, G>, a.ntraj, G * (N / R), res1d_smem<T, N, R>(), s, &a);
 }
 
 template <> int resident1d_max_n<float>() { return 4096; }
