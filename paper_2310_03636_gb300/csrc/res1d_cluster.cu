@@ -26,10 +26,25 @@ __device__ __forceinline__ V twc_rank(V a, int e) {
     return twc16<DIR>(a, (e * (16 / C)) & 15);
 }
 
+// Entries of the local transform's stage-twiddle table kept in shared memory (those of
+// its first twiddled stage; the rest are read through L1), and the block's shared memory:
+// the three component slices and that table head.
+template <typename T, int M, int R>
+constexpr int res1d_cluster_tw_split() {
+    using P = FftPlan<M, R>;
+    return P::kStages > 2 ? P::tw_offset(2) : P::tw_size();
+}
+
+template <typename T, int M, int R>
+constexpr size_t res1d_cluster_smem() {
+    return (size_t)tw_off<T>(3 * smem_ld<T>(M)) * sizeof(cplx<T>) +
+           (size_t)res1d_cluster_tw_split<T, M, R>() * sizeof(twel<T>);
+}
+
 // Blocks per SM the cluster kernel is compiled for: as many as its shared memory allows.
-template <typename T, int M>
+template <typename T, int M, int R>
 constexpr int res1d_cluster_blocks() {
-    const int b = (227 * 1024) / (3 * smem_ld<T>(M) * (int)sizeof(cplx<T>) + 1024);
+    const int b = (227 * 1024) / ((int)res1d_cluster_smem<T, M, R>() + 1024);
     return b < 1 ? 1 : (b > 8 ? 8 : b);
 }
 
@@ -41,7 +56,7 @@ constexpr int res1d_cluster_blocks() {
 // done before the slice is overwritten), local transforms and phase, publish z_rank,
 // barrier, gather the inverse radix-C step, barrier, store the new slice.
 template <typename T, int M, int R, int C>
-__global__ void __launch_bounds__(M / R, res1d_cluster_blocks<T, M>())
+__global__ void __launch_bounds__(M / R, res1d_cluster_blocks<T, M, R>())
 k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, const twel<T>* __restrict__ wn) {
     using V = cplx<T>;
     constexpr int TP = M / R;
@@ -51,12 +66,15 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
     const int rank = (int)cl.block_rank();
     extern __shared__ __align__(128) unsigned char smraw[];
     V* buf = reinterpret_cast<V*>(smraw);                                  // [3][LD]
+    constexpr int SPLIT = res1d_cluster_tw_split<T, M, R>();
+    twel<T>* tws_s = reinterpret_cast<twel<T>*>(buf + tw_off<T>(3 * LD));   // table head
     const int t = threadIdx.x;
     const int traj = blockIdx.x / C;
     V* g = a.ptrs[traj] + rank * M;
     const V* rbuf[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) rbuf[c] = cl.map_shared_rank(buf, c);
+    copy_table(tws_s, tw_local, SPLIT);
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
         for (int i = t; i < M; i += TP) buf[c * LD + spad(i)] = g[c * N + i];
@@ -76,10 +94,10 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
             }
             cl.sync();   // all reads of component c done before it is overwritten
             V* const fb[1] = {buf + c * LD};
-            fft_pencil<M, R, -1, 1, Sync::Block>(v, fb, tw_local, t);
+            fft_pencil_split<M, R, -1, 1, Sync::Block, SPLIT>(v, fb, tws_s, tw_local, t);
 #pragma unroll
             for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[C * (t + m * TP) + rank]);
-            fft_pencil<M, R, +1, 1, Sync::Block>(v, fb, tw_local, t);
+            fft_pencil_split<M, R, +1, 1, Sync::Block, SPLIT>(v, fb, tws_s, tw_local, t);
 #pragma unroll
             for (int m = 0; m < R; ++m) buf[c * LD + spad(t + m * TP)] = v[0][m];
             cl.sync();   // z_rank published
@@ -136,7 +154,7 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
 template <typename T, int M, int R, int C>
 cudaError_t res1d_cluster_n(const Res1DArgs<T>& a, const twel<T>* tw_local, const twel<T>* wn, cudaStream_t s) {
     auto kern = k_res1d_cluster<T, M, R, C>;
-    const size_t smem = (size_t)3 * smem_ld<T>(M) * sizeof(cplx<T>);
+    const size_t smem = res1d_cluster_smem<T, M, R>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
