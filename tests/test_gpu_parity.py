@@ -101,6 +101,22 @@ def test_propagation_fp32(B, shape, ntraj, steps):
     b.close()
 
 
+def test_propagation_fp32_3d_200_steps(B):
+    """FP32 3D at the 200-step bar: the x pass and the tensor-map y and z passes (the z pass
+    is its own kernel) against the oracle, per component."""
+    shape, ntraj, steps, dt, seed = (64, 64, 64), 2, 200, 0.02, 78
+    b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, dt)
+    assert b.tiles(0)[1] != 0      # the contiguous batch takes the tensor-map z pass
+    b.init_noise(seed, MEAN, 0.5)
+    b.step(steps)
+    assert b.sync_status() == B.GPE_OK
+    gpu = b.psi.cpu().numpy().astype(np.complex128)
+    ref = run_oracle(oracle_initial(shape, ntraj, seed), dt, steps, 3)
+    err = rel_l2_per_comp(gpu, ref)
+    assert err <= 1e-4, err
+    b.close()
+
+
 def test_split_calls_and_time_dependent_q(B):
     """q(t) ramp through knots, advanced in uneven chunks: same as the oracle's single run."""
     shape, ntraj, dt, seed = (64, 64), 2, 0.02, 5
@@ -235,6 +251,33 @@ def test_spectra_fp32_vs_oracle_ensemble(B):
     assert np.abs(gS - rS).max() / np.abs(rS).max() <= 1e-3
     gN, rN = spec[:3] / cnt + 0.5, rs[:3] / cnt + 0.5
     assert (np.abs(gN - rN) / np.abs(rN)).max() <= 1e-3
+    b.close()
+
+
+def test_spectra_fp32_512_vs_oracle(B):
+    """FP32 fields on the benchmark grid (512^2): the spectra kernels the bench runs at this
+    size (row FFT, column FFT, radial bins) against the oracle's binned spectra after 200
+    steps, bin means within 1e-3 relative, and the FP64 diagnostics."""
+    wl = W.C2_2D
+    ntraj, steps, seed = 4, 200, W.SEED_BASE
+    b = B.GPEBatch(wl.shape, ntraj, "c64", wl.c0, wl.c1, wl.q, wl.dt)
+    b.init_noise(seed, wl.mean_spinor(), wl.noise_per_mode)
+    b.step(steps)
+    nb, sd = b.layout()
+    acc = b.new_accumulator(1)
+    b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 0)
+    assert b.sync_status() == B.GPE_OK
+    spec, diag = B.unpack_slot(acc, nb, ntraj)
+    ref_psi = run_oracle(oracle_initial(wl.shape, ntraj, seed), wl.dt, steps, 2, wl.c0, wl.c1, wl.q)
+    rs, rd, counts = oracle_observables(ref_psi, 1.0, 2, q=wl.q)
+    assert nb == 363
+    np.testing.assert_array_equal(b.bin_counts(), counts)
+    cnt = counts * ntraj
+    gS, rS = spec[3] / cnt, rs[3] / cnt
+    assert np.abs(gS - rS).max() / np.abs(rS).max() <= 1e-3
+    gN, rN = spec[:3] / cnt + 0.5, rs[:3] / cnt + 0.5
+    assert (np.abs(gN - rN) / np.abs(rN)).max() <= 1e-3
+    np.testing.assert_allclose(diag[:, :3], rd[:, :3], rtol=1e-4)
     b.close()
 
 

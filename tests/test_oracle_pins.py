@@ -517,6 +517,57 @@ def test_radial_bins(shape):
         assert O.bin_counts(shape).sum() == 512 * 512
 
 
+def test_bin_sum_explicit_loop():
+    """Radial bin sums against an explicit loop over modes and leading indices, with values
+    that differ per mode and per leading index (1D, 2D and 3D grids)."""
+    g = np.random.default_rng(91)
+    for lead, shape in (((3,), (16,)), ((2, 3), (8, 8)), ((2,), (4, 4, 4))):
+        vals = g.normal(size=lead + shape)
+        bins = O.radial_bins(shape).numpy()
+        nb = int(bins.max()) + 1
+        want = np.zeros(lead + (nb,))
+        for li in np.ndindex(*lead):
+            for mi in np.ndindex(*shape):
+                want[li + (bins[mi],)] += vals[li + mi]
+        got = O.bin_sum(torch.as_tensor(vals), torch.as_tensor(bins)).numpy()
+        assert got.shape == want.shape
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+        # every mode lands in exactly one bin
+        np.testing.assert_allclose(got.sum(-1), vals.reshape(lead + (-1,)).sum(-1), rtol=1e-12)
+
+
+def test_sf_band_loss_brute_force():
+    """Band loss = mean over trajectories of sum over grid modes with kmin <= |k| <= kmax of
+    S_perp(k), from explicit DFT loops and an integer band rule.  On an 8 x 8 grid with
+    dx = 1/2, |k| = (2 pi / 4) |j| for integer mode vectors j; kmin and kmax are put exactly
+    on |j| = 1 and |j| = 2, so inclusive bounds take 12 modes and exclusive ones 4."""
+    shape, dx, d = (8, 8), 0.5, 2
+    psi = W.random_field(shape, 2, seed=58, scale=0.7)
+    psi[1] *= 1.7     # trajectories differ in size: a sum instead of a mean is off by far more than 2x
+    L = shape[0] * dx
+    dk = 2 * math.pi / L
+    jf = lambda i, n: i if i < n // 2 else i - n
+    S = []
+    for t in range(2):
+        p = psi[t]
+        Fp = math.sqrt(2) * (np.conj(p[0]) * p[1] + np.conj(p[1]) * p[2])
+        S.append(abs(dx ** d * _brute_dft(Fp, dx)) ** 2 / L ** d)
+    for (lo, hi), (mlo, mhi, incl) in (((dk, 2 * dk), (1, 4, True)),
+                                       ((np.nextafter(dk, 9.0), np.nextafter(2 * dk, 0.0)), (1, 4, False))):
+        want = 0.0
+        count = 0
+        for t in range(2):
+            for kk in np.ndindex(*shape):
+                m = sum(jf(kk[a], shape[a]) ** 2 for a in range(d))
+                inside = (mlo <= m <= mhi) if incl else (mlo < m < mhi)
+                if inside:
+                    want += S[t][kk] / 2
+                    count += 1
+        assert count == 2 * (12 if incl else 4)
+        got = float(O.sf_band_loss(T(psi), dx, d, lo, hi))
+        assert abs(got - want) <= 1e-12 * abs(want), (lo, hi, got, want)
+
+
 def test_noise_spectra_closed_form():
     """Initial truncated-Wigner state: n_m(k) = 0 and S_perp(k) = 2 (n + 1/(2 dx^d))
     (flat in k, as the paper's initial structure factor), within statistical errors."""
