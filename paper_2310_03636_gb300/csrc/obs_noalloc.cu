@@ -10,7 +10,9 @@
 //
 // The scratch array is one file-scope __device__ array, so every GPU that loads the
 // library holds it (kMaxPartials doubles, 192 KiB) until the process exits.  Its device
-// address is looked up once per device on the first call made with that device current.
+// address is looked up once per device on the first call made with that device current
+// and kept for the life of the process: after a cudaDeviceReset the module may come back
+// at another address, so the entry point must not be used again in that process.
 // All calls share the array and it keeps the last call's contents; every slot a call
 // reads is written by the same call first, so nothing needs clearing.  Calls that overlap
 // on the same GPU (for instance on two streams with no ordering between them) race on
@@ -105,7 +107,8 @@ k_diag_partials(const cplx<T>* __restrict__ psi, int64_t sites, int64_t nblk, do
 
 // Per trajectory: the block sums in fixed order, times dx^d, into out[traj * 8 ...] as
 // (N_1, N_0, N_-1, 0, E_q, E_c0, E_c1, 0) -- the record layout of observables_accumulate
-// with the kinetic energy left at zero.
+// with the kinetic energy (slot 3) and the potential energy (slot 7) always zero: this
+// entry point takes no potential and does no transform.
 __global__ void __launch_bounds__(kNaThreads)
 k_diag_final(const double* __restrict__ scratch, int64_t nblk, double vol, double* __restrict__ out) {
     __shared__ double sm[kNaSums * 32];
@@ -138,16 +141,26 @@ extern "C" gpe_status gpe_diagnostics_noalloc(const void* psi, int32_t ntraj, in
                                               double* out, void* stream) {
     using namespace gpe;
     if (!psi || !out || !n) return set_error(GPE_EINVAL, "gpe_diagnostics_noalloc: NULL psi, out or n");
+    // An error left pending by earlier, unrelated work is not this call's to report or clear.
+    if (cudaPeekAtLastError() != cudaSuccess)
+        return set_error(GPE_ECUDA, "gpe_diagnostics_noalloc: a CUDA error from earlier work is pending");
     if (ndim < 1 || ndim > 3 || ntraj <= 0 || !(dx > 0.0))
         return set_error(GPE_EINVAL, "gpe_diagnostics_noalloc: need 1 <= ndim <= 3, ntraj > 0, dx > 0");
     if (dtype != GPE_C64 && dtype != GPE_C128) return set_error(GPE_EINVAL, "gpe_diagnostics_noalloc: bad dtype");
     if (((uintptr_t)psi & 15u) || ((uintptr_t)out & 7u))
         return set_error(GPE_EINVAL, "gpe_diagnostics_noalloc: psi must be 16-byte and out 8-byte aligned");
+    // Capacity in sites, checked after every factor so the product cannot overflow
+    // (each factor is below 2^31 and the running product stays below 2^24 x 4096).
+    constexpr int64_t kMaxSites = kMaxPartialBlocks * kNaSitesPerBlock;
     int64_t sites = 1;
     for (int a = 0; a < 3; ++a) {
         if ((a < ndim && n[a] < 1) || (a >= ndim && n[a] != 1))
             return set_error(GPE_EINVAL, "gpe_diagnostics_noalloc: n[a] >= 1 on used axes, 1 on unused axes");
         sites *= n[a];
+        if (sites > kMaxSites)
+            return set_error(GPE_EINVAL,
+                             "gpe_diagnostics_noalloc: ntraj * ceil(sites / 4096) exceeds the fixed scratch "
+                             "capacity of 4096 site blocks");
     }
     const int64_t nblk = (sites + kNaSitesPerBlock - 1) / kNaSitesPerBlock;
     // Sizes beyond the fixed scratch array are rejected: ntraj * ceil(sites / 4096) must
@@ -180,8 +193,10 @@ extern "C" gpe_status gpe_diagnostics_noalloc(const void* psi, int32_t ntraj, in
     else
         k_diag_partials<double><<<dim3((unsigned)nblk, ntraj), kNaThreads, 0, s>>>(
             static_cast<const double2*>(psi), sites, nblk, c0, c1, q, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(GPE_ECUDA, cudaGetErrorString(e));
     k_diag_final<<<ntraj, kNaThreads, 0, s>>>(scratch, nblk, vol, out);
-    const cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(GPE_ECUDA, cudaGetErrorString(e));
     return GPE_OK;
 }
