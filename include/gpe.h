@@ -180,6 +180,23 @@ gpe_status gpe_batch_set_integrator(gpe_batch* batch, int32_t kind);
  * profiling is enabled. */
 gpe_status gpe_batch_set_graph(gpe_batch* batch, int32_t enable);
 
+/* Test hook for the bounded waits (failure handling; the paper has no counterpart).  Sets
+ * how many times the first wait of each block of the x pass and of the tensor-map
+ * strided pass may poll its copy barrier before the wait counts as expired: -1 restores
+ * the default (2^22 polls), 0 makes that wait expire at once.  An expired wait records
+ * GPE_ETIMEOUT in the status word (read by gpe_sync_status); the block then waits, with
+ * the default limit, for its copies in flight and returns without writing, so that step's
+ * fields are not a valid result.  Drops the batch's captured graphs.  Errors: GPE_EINVAL
+ * (NULL batch, value below -1 or not below 2^32 - 1). */
+gpe_status gpe_batch_set_wait_limit(gpe_batch* batch, int64_t first_wait_polls);
+
+/* Test hook for the allocation-failure paths (the paper has no counterpart): after
+ * ``after`` more successful device allocations by this library (any batch, any thread),
+ * the next one fails as if the device were out of memory -- the call that needed it
+ * returns GPE_ENOMEM -- and the hook switches itself off; after < 0 switches it off.
+ * Always returns GPE_OK. */
+gpe_status gpe_debug_fail_alloc(int64_t after);
+
 /* Tile autotuner of the strided (y, z) kinetic passes (the paper prescribes none; the
  * choice changes no result bit).  Enabled by default: the first gpe_step_batch call of an
  * FP32 batch times, per shape group with back-to-back fields, every tile width (complex
@@ -244,13 +261,17 @@ gpe_status gpe_profile_read(gpe_batch* batch, double* ms, int64_t* launches);
  * back, each [3][n2][n1][n0] complex (dtype), 16-byte aligned.  out: caller-owned device
  * array of ntraj * 8 doubles, overwritten (not accumulated) with
  * (N_1, N_0, N_-1, 0, E_q, E_c0, E_c1, 0) per trajectory -- the diagnostics record of
- * observables_accumulate without the kinetic energy.  Partial sums live in a fixed
+ * observables_accumulate with the kinetic energy (slot 3) and the potential energy
+ * (slot 7) always zero: no potential is taken, even for fields of a batch that has one.
+ * Any extents are accepted (not only powers of two).  Partial sums live in a fixed
  * 192 KiB array compiled into the library (held on every device that loads it until the
  * process exits); capacity: ntraj * ceil(sites / 4096) <= 4096 site blocks, larger
  * requests return GPE_EINVAL with a message.  The first call on a device looks up the
- * array's device address, so make it before any stream capture.  Calls share the array:
- * calls that overlap on the same GPU race; serialise them.  Errors: GPE_EINVAL (NULL or
- * misaligned pointers, bad sizes, capacity), GPE_ECUDA. */
+ * array's device address, so make it before any stream capture; the address is kept for
+ * the process's life, so after a cudaDeviceReset the entry point must not be called
+ * again.  Calls share the array: calls that overlap on the same GPU race; serialise them.
+ * Errors: GPE_EINVAL (NULL or misaligned pointers, bad sizes, capacity), GPE_ECUDA (also
+ * when an error from earlier work is already pending; it is left for its owner). */
 gpe_status gpe_diagnostics_noalloc(const void* psi, int32_t ntraj, int32_t ndim, const int32_t n[3],
                                    double dx, gpe_dtype dtype, double c0, double c1, double q,
                                    double* out, void* stream);

@@ -62,6 +62,8 @@ def _load():
         "gpe_sf_band_loss": ([vp, vp, dbl, dbl, vp, vp, vp], ctypes.c_int),
         "gpe_launch_count": ([], i64),
         "gpe_batch_set_graph": ([vp, i32], ctypes.c_int),
+        "gpe_batch_set_wait_limit": ([vp, i64], ctypes.c_int),
+        "gpe_debug_fail_alloc": ([i64], ctypes.c_int),
         "gpe_batch_set_integrator": ([vp, i32], ctypes.c_int),
         "gpe_batch_set_traj_base": ([vp, i64], ctypes.c_int),
         "gpe_batch_set_potential": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
@@ -331,6 +333,11 @@ class GPEBatch:
 
     def set_graph(self, enable=True):
         _check(LIB.gpe_batch_set_graph(self.h, 1 if enable else 0))
+
+    def set_wait_limit(self, first_wait_polls=-1):
+        """Poll limit of each pass block's first copy wait (-1: the default; 0 expires it at
+        once, a test of the timeout path)."""
+        _check(LIB.gpe_batch_set_wait_limit(self.h, int(first_wait_polls)))
 
     def set_autotune(self, enable=True):
         _check(LIB.gpe_batch_set_autotune(self.h, 1 if enable else 0))

@@ -49,8 +49,9 @@ int colpass_tma_candidates<float>(int n, int* cols) {
 template <>
 cudaError_t launch_colpass_tma<float>(int n, int axis, int cols, const CUtensorMap& map, int n_tiles, int nx_tiles,
                                       int ny, const twel<float>* tws[3], const twel<float>* ph, int* status,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, uint32_t wait_first) {
     ColTmaArgs<float> a{};
+    a.wait_first = wait_first;
     a.n_tiles = n_tiles;
     a.nx_tiles = nx_tiles;
     a.ny = ny;

@@ -44,6 +44,10 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 std::atomic<int64_t> g_launches{0};
 
+// Allocation-failure test hook: number of device allocations still allowed to succeed
+// before one fails (-1: off).
+std::atomic<int64_t> g_alloc_fail_after{-1};
+
 constexpr int kProfKinds = 6;
 
 struct Profiler {
@@ -64,6 +68,21 @@ struct Profiler {
 }  // namespace
 
 void gpe::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+cudaError_t gpe::device_malloc(void** p, size_t bytes) {
+    int64_t left = g_alloc_fail_after.load();
+    while (left >= 0) {
+        // the hook counts down once per allocation; at zero this one fails and it switches off
+        if (g_alloc_fail_after.compare_exchange_weak(left, left - 1)) {
+            if (left == 0) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 
 namespace {
 
@@ -132,6 +151,7 @@ struct gpe_batch {
     int integrator = 0;               // GPE_INTEGRATOR_PAPER or GPE_INTEGRATOR_ROTATION
     bool autotune = true;             // time the column-pass tile widths on the first step
     int64_t traj_base = 0;            // added to batch indices in the noise counter
+    uint32_t wait_first = 0;          // first copy wait's poll limit of the passes (0: default, else 1 + limit)
     int* d_status = nullptr;
     int device = 0;
     std::vector<void*> allocs;
@@ -234,7 +254,7 @@ std::vector<twel<T>> stage_twiddles_host(int n, int R) {
 }
 
 gpe_status dev_alloc(gpe_batch* b, void** p, size_t bytes) {
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = device_malloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(GPE_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
@@ -326,6 +346,7 @@ PassArgs<T> base_args(const gpe_batch* b, const Group& g) {
     a.coef.dt = (T)b->p.dt;
     a.coef.q = (T)b->p.q;
     a.coef.kind = b->integrator;
+    a.wait_first = b->wait_first;
     return a;
 }
 
@@ -342,7 +363,7 @@ cudaError_t col_pass(gpe_batch* b, const Group& g, int ax, bool half, cudaStream
                                  reinterpret_cast<const twel<T>*>(g.tw[ax][2])};
         return launch_colpass_tma<T>(g.n[ax], ax, g.cols[ax], ax == 1 ? g.map_y : g.map_z, n_tiles, nxt, ny, tws,
                                      reinterpret_cast<const twel<T>*>(half ? g.ph_half[ax] : g.ph_full[ax]),
-                                     b->d_status, s);
+                                     b->d_status, s, b->wait_first);
     }
     PassArgs<T> a = base_args<T>(b, g);
     for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[ax][ri]);
@@ -446,7 +467,7 @@ gpe_status tune_tiles(gpe_batch* b, cudaStream_t s) {
         const size_t cap = ((size_t)256 << 20) / per_traj;
         const int nt = (int)std::min<size_t>((size_t)g.ntraj, cap < 1 ? 1 : cap);
         void* scratch = nullptr;
-        if (cudaMalloc(&scratch, per_traj * nt) != cudaSuccess) {
+        if (device_malloc(&scratch, per_traj * nt) != cudaSuccess) {
             cudaGetLastError();
             continue;   // no room to tune: keep the defaults
         }
@@ -1055,6 +1076,21 @@ gpe_status gpe_batch_get_tiles(const gpe_batch* b, int32_t traj, int32_t cols[2]
                 return GPE_OK;
             }
     return fail(GPE_EINVAL, "trajectory %d not found", traj);
+}
+
+gpe_status gpe_batch_set_wait_limit(gpe_batch* b, int64_t first_wait_polls) {
+    g_err.clear();
+    if (!b) return fail(GPE_EINVAL, "batch is NULL");
+    if (first_wait_polls < -1 || first_wait_polls >= (int64_t)0xFFFFFFFFu)
+        return fail(GPE_EINVAL, "first_wait_polls must be -1 (default) or in [0, 2^32 - 1)");
+    b->wait_first = first_wait_polls < 0 ? 0u : (uint32_t)(first_wait_polls + 1);
+    drop_graphs(b);
+    return GPE_OK;
+}
+
+gpe_status gpe_debug_fail_alloc(int64_t after) {
+    g_alloc_fail_after.store(after < 0 ? -1 : after);
+    return GPE_OK;
 }
 
 gpe_status gpe_batch_set_graph(gpe_batch* b, int32_t enable) {

@@ -35,6 +35,7 @@ struct PassArgs {
     LocalCoef<T> coef;        // couplings for the local step (row pass)
     const T* vpot;            // row pass: potential [3][sites] shared by the group, or null
     int* status;              // device status word (bounded waits that expire)
+    uint32_t wait_first;      // row pass: 0 = default limit of the first copy wait, else 1 + its poll limit
 };
 
 template <typename T>
@@ -95,6 +96,10 @@ struct Group {
 // Sets the message gpe_last_error() returns on this thread.
 void set_last_error(const char* msg);
 
+// Every device allocation of the library goes through here, so that a test hook
+// (gpe_debug_fail_alloc) can make one fail as if the device were out of memory.
+cudaError_t device_malloc(void** p, size_t bytes);
+
 template <typename T> int xpass_max_n();
 template <typename T> int colpass_max_n();
 template <typename T> int resident1d_max_n();
@@ -119,7 +124,8 @@ int colpass_cols(int n);
 // complex columns wide (one of colpass_tma_candidates; the map's box must match).
 template <typename T>
 cudaError_t launch_colpass_tma(int n, int axis, int cols, const CUtensorMap& map, int n_tiles, int nx_tiles,
-                               int ny, const twel<T>* tw4_8_16[3], const twel<T>* ph, int* status, cudaStream_t s);
+                               int ny, const twel<T>* tw4_8_16[3], const twel<T>* ph, int* status, cudaStream_t s,
+                               uint32_t wait_first = 0);
 // Tile widths the column pass is built for at pencil length n (written to cols[0..]).
 template <typename T>
 int colpass_tma_candidates(int n, int* cols);

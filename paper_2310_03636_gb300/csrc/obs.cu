@@ -357,10 +357,12 @@ gpe_status obs_init(ObsWork& w, const std::vector<Group>& groups, bool f64, int)
     for (int b = 0; b < w.nbins; ++b) off[b + 1] = off[b] + (int32_t)w.counts[b];
     std::vector<int32_t> fill(off.begin(), off.end() - 1);
     for (int64_t i = 0; i < g.sites; ++i) modes[fill[bin[i]]++] = (int32_t)i;
-    cudaError_t e = cudaMalloc(&w.d_off, sizeof(int32_t) * (w.nbins + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_modes, sizeof(int32_t) * g.sites);
+    cudaError_t e = device_malloc((void**)&w.d_off, sizeof(int32_t) * (w.nbins + 1));
+    if (e == cudaSuccess) e = device_malloc((void**)&w.d_modes, sizeof(int32_t) * g.sites);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        cudaFree(w.d_off);
+        w.d_off = nullptr;
         return obs_fail(GPE_ENOMEM, "bin tables", e);
     }
     e = cudaMemcpy(w.d_off, off.data(), sizeof(int32_t) * (w.nbins + 1), cudaMemcpyHostToDevice);
@@ -391,12 +393,21 @@ static gpe_status ensure_workspace(ObsWork& w, const std::vector<Group>& groups)
     const int64_t budget = (int64_t)1 << 30;
     w.chunk = std::max<int64_t>(1, std::min<int64_t>(max_traj, budget / per_traj));
     w.nblk = (max_sites + kSitesPerBlock - 1) / kSitesPerBlock;
-    cudaError_t e = cudaMalloc(&w.d_W, (size_t)(w.chunk * per_traj));
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_Wptrs, sizeof(void*) * w.chunk);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_part, sizeof(double) * w.chunk * w.nblk * kPartVals);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_ekin, sizeof(double) * w.chunk * w.nblk * 3);
+    cudaError_t e = device_malloc(&w.d_W, (size_t)(w.chunk * per_traj));
+    if (e == cudaSuccess) e = device_malloc((void**)&w.d_Wptrs, sizeof(void*) * w.chunk);
+    if (e == cudaSuccess) e = device_malloc((void**)&w.d_part, sizeof(double) * w.chunk * w.nblk * kPartVals);
+    if (e == cudaSuccess) e = device_malloc((void**)&w.d_ekin, sizeof(double) * w.chunk * w.nblk * 3);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        // free the part that was allocated: a later call starts over
+        cudaFree(w.d_W);
+        cudaFree(w.d_Wptrs);
+        cudaFree(w.d_part);
+        cudaFree(w.d_ekin);
+        w.d_W = nullptr;
+        w.d_Wptrs = nullptr;
+        w.d_part = nullptr;
+        w.d_ekin = nullptr;
         return obs_fail(GPE_ENOMEM, "observables workspace", e);
     }
     std::vector<void*> ptrs(w.chunk);

@@ -104,9 +104,10 @@ int colpass_tma_candidates<double>(int n, int* cols) {
 template <>
 cudaError_t launch_colpass_tma<double>(int n, int axis, int cols, const CUtensorMap& map, int n_tiles, int nx_tiles,
                                        int ny, const twel<double>* tws[3], const twel<double>* ph, int* status,
-                                       cudaStream_t s) {
+                                       cudaStream_t s, uint32_t wait_first) {
     if (cols != Tune<double>::kColCols(n)) return cudaErrorInvalidValue;
     ColTmaArgs<double> a{};
+    a.wait_first = wait_first;
     a.n_tiles = n_tiles;
     a.nx_tiles = nx_tiles;
     a.ny = ny;

@@ -55,6 +55,13 @@ template <int N, int R> constexpr int xpass_rows() {
 
 constexpr uint32_t kWaitLimit = 1u << 22;   // mbarrier polls before a wait counts as expired
 
+// Poll limit of a block's first copy wait: the default, or the value a test set
+// (wait_first = 1 + limit; 0 keeps the default).  Later waits and the drain after an
+// expired wait always take the default.
+__host__ __device__ constexpr uint32_t first_wait_limit(uint32_t wait_first) {
+    return wait_first == 0 ? kWaitLimit : wait_first - 1;
+}
+
 // FFT along x of one row-component held in shared memory (thread t owns positions
 // t + m TP), times a phase table, inverse FFT, back into shared memory.  A row of at most
 // 32 threads lies within one warp, so its exchanges synchronise the warp only.
@@ -109,7 +116,7 @@ k_xpass(const PassArgs<T> a) {
         }
     }
     copy_table(tws, a.tw[tw_slot<R>()], TWN);
-    const bool ok = __syncthreads_and(mbar_wait(bar, 0, kWaitLimit));
+    const bool ok = __syncthreads_and(mbar_wait(bar, 0, first_wait_limit(a.wait_first)));
     if (!ok) {
         if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)GPE_ETIMEOUT);
         mbar_wait(bar, 0, kWaitLimit);
@@ -229,6 +236,7 @@ struct ColTmaArgs {
     const twel<T>* tw;   // stage twiddles of FftPlan<N, R>
     const twel<T>* ph;   // phase table (unused when FWD_ONLY)
     int* status;
+    uint32_t wait_first; // 0 = default poll limit of each block's first wait, else 1 + that limit
 };
 
 // Elements of one tile buffer: the tile ([N][COLS], as the TMA engine writes it) and,
@@ -311,12 +319,15 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
     copy_table(tws, a.tw, TWN);
     __syncthreads();
     int it = 0;
-    bool ok = true;
+    int failed_tile = -1;
     for (int tile = first; tile < a.n_tiles; tile += stride, ++it) {
         const int st = it & 1;
         V* bs = buf + st * SB;
-        ok = __syncthreads_and(mbar_wait(&bar[st], (uint32_t)((it >> 1) & 1), kWaitLimit));
-        if (!ok) break;
+        const uint32_t lim = it == 0 ? first_wait_limit(a.wait_first) : kWaitLimit;
+        if (!__syncthreads_and(mbar_wait(&bar[st], (uint32_t)((it >> 1) & 1), lim))) {
+            failed_tile = tile;
+            break;
+        }
         V v[1][R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[0][m] = bs[(t + m * TP) * COLS + col];
@@ -346,11 +357,14 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
         }
     }
     if (threadIdx.x == 0) {
-        if (!ok) {
+        if (failed_tile >= 0) {
             atomicCAS(a.status, 0, (int)GPE_ETIMEOUT);
-            // let copies still in flight land before the block's shared memory goes away
+            // Let the loads still in flight land before the block's shared memory goes away:
+            // the one the expired wait was for and, if it was issued, the next tile's (loads
+            // run two tiles ahead, so that one exists exactly when the next tile does).
             mbar_wait(&bar[it & 1], (uint32_t)((it >> 1) & 1), kWaitLimit);
-            mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
+            if (failed_tile + stride < a.n_tiles)
+                mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimit);
         }
         bulk_wait_all();
     }

@@ -35,3 +35,11 @@ def test_traffic_figures_follow_the_sources():
         assert bench.ncu_traffic("xpass") == float(d["per_launch_bytes"]["xpass"])
     else:
         assert bench.ncu_traffic("xpass") is None
+
+
+def test_step_stats_median_and_spread():
+    s = bench.step_stats([10.0, 12.0, 11.0, 30.0, 11.5])
+    assert s["n"] == 5 and s["median_ms"] == 11.5 and s["min_ms"] == 10.0 and s["max_ms"] == 30.0
+    assert abs(s["spread_pct"] - 100.0 * 20.0 / 11.5) < 1e-12
+    assert s["p10_ms"] == 10.0 and s["p90_ms"] == 30.0
+    assert bench.step_stats([]) is None
