@@ -11,9 +11,16 @@ template <> struct cplx_sel<float> { using type = float2; };
 template <> struct cplx_sel<double> { using type = double2; };
 template <typename T> using cplx = typename cplx_sel<T>::type;
 
-// Table entry for twiddles and phase factors: FP32 tables carry each constant as a
-// hi + lo pair (hi = fl(c), lo = fl(c - hi)), so the rounding of the constant itself,
-// which would repeat identically in every step, drops to O(eps^2); FP64 tables hold c.
+// Table entry for twiddles and phase factors c = m e^{i phi} (m = 1 for twiddles, 1/N for
+// the kinetic phases).  FP64 tables hold c.  FP32 tables hold the rotation in three-shear
+// ("lifting") form: phi is reduced by a multiple j of pi to phi' in [-pi/2, pi/2], and the
+// entry is (p, u, s, 0) with p = -tan(phi'/2), u = sin(phi'), s = (-1)^j m, each computed in
+// FP64 and rounded once.  The rotation is applied as x += p y; y += u x; x += p y (three
+// fmas) and scaled by s.  The three shears have determinant exactly 1 whatever the rounding
+// of p and u, so the map preserves area: its mean gain in |w|^2 over the phase of w is
+// 1 + O(eps^2), whereas an FP32 pair (fl(cos), fl(sin)) scales |w|^2 by a fixed
+// 1 + O(eps) that repeats in every step and accumulates.  The angle error is relative
+// (O(eps phi)), so small kinetic phases stay exact to FP32 precision.
 template <typename T> struct tw_sel;
 template <> struct tw_sel<float> { using type = float4; };
 template <> struct tw_sel<double> { using type = double2; };
@@ -41,32 +48,32 @@ template <typename V, typename T> __device__ __forceinline__ V cscale(V a, T s) 
 template <typename V> __device__ __forceinline__ V cmul_mi(V a) { return mk(a.y, -a.x); }
 template <typename V> __device__ __forceinline__ auto cabs2(V a) { return a.x * a.x + a.y * a.y; }
 
-// w * f (DIR < 0) or w * conj(f) (DIR > 0) with f a table entry.
-template <int DIR>
-__device__ __forceinline__ float2 twmul(float2 w, float4 f) {
-    const float fy = DIR < 0 ? f.y : -f.y, ly = DIR < 0 ? f.w : -f.w;
-    const float sr = fmaf(w.x, f.z, -w.y * ly);
-    const float si = fmaf(w.x, ly, w.y * f.z);
-    return mk(fmaf(w.x, f.x, fmaf(-w.y, fy, sr)), fmaf(w.x, fy, fmaf(w.y, f.x, si)));
+// w e^{i phi} by three shears (p = -tan(phi/2), u = sin(phi), |phi| <= pi/2).
+__device__ __forceinline__ float2 lift_rot(float2 w, float p, float u) {
+    const float x1 = fmaf(p, w.y, w.x);
+    const float y1 = fmaf(u, x1, w.y);
+    return make_float2(fmaf(p, y1, x1), y1);
 }
-template <int DIR>
+
+// w * f (DIR < 0) or w * conj(f) (DIR > 0) with f a table entry.  SIG = false skips the
+// factor s where the caller knows every entry it reads has s = +1 (angles within +-pi/2,
+// unit modulus).
+template <int DIR, bool SIG = true>
+__device__ __forceinline__ float2 twmul(float2 w, float4 f) {
+    const float2 r = lift_rot(w, DIR < 0 ? f.x : -f.x, DIR < 0 ? f.y : -f.y);
+    if constexpr (SIG) return make_float2(r.x * f.z, r.y * f.z);
+    return r;
+}
+template <int DIR, bool SIG = true>
 __device__ __forceinline__ double2 twmul(double2 w, double2 f) {
     const double fy = DIR < 0 ? f.y : -f.y;
     return mk(w.x * f.x - w.y * fy, w.x * fy + w.y * f.x);
 }
 
-// The same product for a kinetic phase-table entry, with the cosine products w f.x as the
-// outer fma of both components.  The kinetic phases of the IR modes are small angles: there
-// f.x_hi is 1 or a few ulps below it, so w.y f.x_hi is (nearly) a float, and an inner fma
-// that adds the small lo terms to it would round them away in the same direction every
-// step, growing |w f| (twmul's imaginary part has that order; near +-pi/2 this one has
-// the weakness instead, which the phases of the modes that carry the norm do not reach).
+// The same product for a kinetic phase-table entry (scale 1/N included).
 template <int DIR>
 __device__ __forceinline__ float2 phmul(float2 w, float4 f) {
-    const float fy = DIR < 0 ? f.y : -f.y, ly = DIR < 0 ? f.w : -f.w;
-    const float sr = fmaf(w.x, f.z, -w.y * ly);
-    const float si = fmaf(w.x, ly, w.y * f.z);
-    return mk(fmaf(w.x, f.x, fmaf(-w.y, fy, sr)), fmaf(w.y, f.x, fmaf(w.x, fy, si)));
+    return twmul<DIR, true>(w, f);
 }
 template <int DIR>
 __device__ __forceinline__ double2 phmul(double2 w, double2 f) {

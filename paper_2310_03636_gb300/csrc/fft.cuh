@@ -9,10 +9,11 @@
 // first stage of the inverse transform needs, so a momentum-space phase multiply sits
 // between them without a shared-memory round trip.
 //
-// Twiddle factors come from tables computed in FP64; FP32 tables hold hi + lo pairs so
-// that the constants carry no O(eps) bias (their rounding error would otherwise repeat
-// identically in every time step and accumulate linearly).  Transforms are unnormalised
-// (the 1/N goes into the phase table).
+// Twiddle factors come from tables computed in FP64.  In FP32 every rotation -- table
+// twiddles and the constant rotations inside the radix-8/16 butterflies -- is applied as
+// three shears with determinant exactly 1 (common.cuh), so the rounding of the constants
+// carries no O(eps) bias in |w| (a bias would repeat identically in every time step and
+// accumulate linearly).  Transforms are unnormalised (the 1/N goes into the phase table).
 #pragma once
 
 #include "common.cuh"
@@ -39,7 +40,9 @@ __host__ __device__ constexpr double cos16(int e) {
          : 0.92387953251128675613;
 }
 
-// a * exp(DIR 2 pi i e / 16), e a compile-time constant after unrolling.
+// a * exp(DIR 2 pi i e / 16), e a compile-time constant after unrolling.  FP32: the
+// rotation is reduced by a multiple of pi to at most 3 pi / 8 (the multiple becomes a sign,
+// folded into the callers' adds) and applied as three shears with FP64-computed constants.
 template <int DIR, typename V>
 __device__ __forceinline__ V twc16(V a, int e) {
     using T = decltype(a.x);
@@ -48,6 +51,25 @@ __device__ __forceinline__ V twc16(V a, int e) {
     if (e == 8) return mk(-a.x, -a.y);
     if (e == 4) return DIR < 0 ? mk(a.y, -a.x) : mk(-a.y, a.x);
     if (e == 12) return DIR < 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
+    if constexpr (sizeof(T) == 4) {
+        // angle j pi / 8 with j = DIR e folded into (-8, 8], then into (-4, 4) and a sign
+        int j = DIR < 0 ? -e : e;
+        if (j > 8) j -= 16;
+        if (j <= -8) j += 16;
+        bool neg = false;
+        if (j > 4) { j -= 8; neg = true; }
+        if (j < -4) { j += 8; neg = true; }
+        const int aj = j < 0 ? -j : j;
+        const double th = aj == 1 ? 0.19891236737965800691      // tan(pi / 16)
+                        : aj == 2 ? 0.41421356237309504880      // tan(pi / 8)
+                                  : 0.66817863791929891999;     // tan(3 pi / 16)
+        const double sn = aj == 1 ? 0.38268343236508977173      // sin(pi / 8)
+                        : aj == 2 ? 0.70710678118654752440      // sin(pi / 4)
+                                  : 0.92387953251128675613;     // sin(3 pi / 8)
+        const float p = (float)(j < 0 ? th : -th), u = (float)(j < 0 ? -sn : sn);
+        const float2 r = lift_rot(a, p, u);
+        return neg ? mk(-r.x, -r.y) : r;
+    }
     const double cr = cos16(e);
     const double ci = DIR * cos16(e + 12);
     if ((e & 1) == 0) {
@@ -182,8 +204,12 @@ __device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC
                 TW f;
                 if constexpr (SPLIT > 0 && OFF >= SPLIT) f = tws_hi[OFF + (r - 1) * NS + k];
                 else f = tws[OFF + (r - 1) * NS + k];
+                // if every twiddle angle 2 pi r k / (NS RS) of this r is within pi/2, the
+                // table's sign is +1 and the scale is skipped (r is a constant once unrolled)
+                const bool sig = 4 * r * (NS - 1) > NS * RS;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) w[c][r] = twmul<DIR>(w[c][r], f);
+                for (int c = 0; c < NC; ++c)
+                    w[c][r] = sig ? twmul<DIR, true>(w[c][r], f) : twmul<DIR, false>(w[c][r], f);
             }
         }
 #pragma unroll

@@ -203,11 +203,24 @@ struct ProfScope {
 namespace {
 
 // Kinetic phase tables exp(-i tau k^2/2) / n for tau = dt and dt/2, computed in FP64.
-// Table entry from an FP64 complex value: FP32 keeps hi = fl(c) and lo = fl(c - hi).
+// Table entry from an FP64 complex value c = m e^{i phi}.  FP32 keeps the three-shear form
+// of the rotation (common.cuh): phi reduced by a multiple j of pi into [-pi/2, pi/2] (with a
+// margin of 1e-12 so angles that are exactly +-pi/2 keep j = 0), then (-tan(phi/2), sin(phi),
+// (-1)^j m, 0), each rounded once from FP64.
 template <typename T> twel<T> tw_entry(double re, double im);
 template <> float4 tw_entry<float>(double re, double im) {
-    const float hr = (float)re, hi = (float)im;
-    return make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+    const double pi = 3.14159265358979323846, half_pi = 1.57079632679489661923;
+    const double m = std::hypot(re, im);
+    double phi = std::atan2(im, re);
+    double s = m;
+    if (phi > half_pi + 1e-12) {
+        phi -= pi;
+        s = -m;
+    } else if (phi < -half_pi - 1e-12) {
+        phi += pi;
+        s = -m;
+    }
+    return make_float4((float)(-std::tan(0.5 * phi)), (float)std::sin(phi), (float)s, 0.0f);
 }
 template <> double2 tw_entry<double>(double re, double im) { return make_double2(re, im); }
 
