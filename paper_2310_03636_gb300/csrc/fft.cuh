@@ -143,11 +143,21 @@ __host__ __device__ constexpr int smem_ld(int n) {
                (int)(128 / (2 * sizeof(T))) + 1;
 }
 
-enum class Sync { Block, Warp };
+// Who synchronises a pencil's exchanges: the whole block, one warp (pencils of at most
+// 32 threads), or the pencil's own group of threads (a named barrier per group of TP
+// consecutive threads, TP a multiple of 32, at most 15 groups per block), so that the
+// pencils of one block do not wait for each other.
+enum class Sync { Block, Warp, Group };
 
-template <Sync SY> __device__ __forceinline__ void pencil_sync() {
-    if constexpr (SY == Sync::Block) __syncthreads();
-    else __syncwarp(blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u));
+template <Sync SY, int TP = 0> __device__ __forceinline__ void pencil_sync() {
+    if constexpr (SY == Sync::Block) {
+        __syncthreads();
+    } else if constexpr (SY == Sync::Group) {
+        static_assert(TP % 32 == 0 && TP >= 64, "group barriers need whole warps");
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / TP)), "r"(TP) : "memory");
+    } else {
+        __syncwarp(blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u));
+    }
 }
 
 // Stage plan of a length-N transform with R points per thread: stages of radix R, then
@@ -228,12 +238,12 @@ __device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC
         }
     }
     if constexpr (!LAST) {
-        pencil_sync<SY>();
+        pencil_sync<SY, TP>();
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int m = 0; m < R; ++m) v[c][m] = buf[c][spad(t + m * TP)];
-        pencil_sync<SY>();
+        pencil_sync<SY, TP>();
     }
 }
 

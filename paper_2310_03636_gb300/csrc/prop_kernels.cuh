@@ -64,8 +64,9 @@ __host__ __device__ constexpr uint32_t first_wait_limit(uint32_t wait_first) {
 
 // FFT along x of one row-component held in shared memory (thread t owns positions
 // t + m TP), times a phase table, inverse FFT, back into shared memory.  A row of at most
-// 32 threads lies within one warp, so its exchanges synchronise the warp only.
-template <typename T, int N, int R>
+// 32 threads lies within one warp, so its exchanges synchronise the warp only; the rows
+// of a block with several larger rows synchronise with a barrier of their own.
+template <typename T, int N, int R, int RPC = 1>
 __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const twel<T>* tws,
                                             const twel<T>* __restrict__ ph, int t) {
     using V = cplx<T>;
@@ -74,7 +75,7 @@ __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const t
     V* const xb[1] = {xbuf};
 #pragma unroll
     for (int m = 0; m < R; ++m) v[0][m] = row[t + m * TP];
-    constexpr Sync SY = TP <= 32 ? Sync::Warp : Sync::Block;
+    constexpr Sync SY = TP <= 32 ? Sync::Warp : (RPC > 1 ? Sync::Group : Sync::Block);
     fft_pencil<N, R, -1, 1, SY>(v, xb, tws, t);
 #pragma unroll
     for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
@@ -126,10 +127,27 @@ k_xpass(const PassArgs<T> a) {
     V* Xr = X + lrow * LD;
     if constexpr (PRE) {
 #pragma unroll 1
-        for (int c = 0; c < 3; ++c) kinetic_row<T, N, R>(Dr + c * N, Xr, tws, a.ph_pre, t);
+        for (int c = 0; c < 3; ++c) kinetic_row<T, N, R, RPC>(Dr + c * N, Xr, tws, a.ph_pre, t);
     }
     if (lrow < nrows) {
-        if (a.vpot == nullptr) {
+        if (sizeof(T) == 4 && a.vpot == nullptr && a.coef.kind == 0) {
+            // the FP32 step of the paper's scheme two sites at a time (packed instructions)
+            if constexpr (sizeof(T) == 4) {
+#pragma unroll 1
+                for (int m = 0; m < R; m += 2) {
+                    const int i = t + m * TP, j = i + TP;
+                    cpair p1 = pack_pair(Dr[i], Dr[j]), p0 = pack_pair(Dr[N + i], Dr[N + j]),
+                          pm = pack_pair(Dr[2 * N + i], Dr[2 * N + j]);
+                    local_step_pair(p1, p0, pm, a.coef);
+                    Dr[i] = lane_x(p1);
+                    Dr[j] = lane_y(p1);
+                    Dr[N + i] = lane_x(p0);
+                    Dr[N + j] = lane_y(p0);
+                    Dr[2 * N + i] = lane_x(pm);
+                    Dr[2 * N + j] = lane_y(pm);
+                }
+            }
+        } else if (a.vpot == nullptr) {
 #pragma unroll 2
             for (int m = 0; m < R; ++m) {
                 const int i = t + m * TP;
@@ -155,7 +173,7 @@ k_xpass(const PassArgs<T> a) {
         }
     }
 #pragma unroll 1
-    for (int c = 0; c < 3; ++c) kinetic_row<T, N, R>(Dr + c * N, Xr, tws, a.ph, t);
+    for (int c = 0; c < 3; ++c) kinetic_row<T, N, R, RPC>(Dr + c * N, Xr, tws, a.ph, t);
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
