@@ -538,6 +538,8 @@ def run_other(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    if args.workload == "ragged":
+        extra["scheduling"] = ragged_scheduling_bound(B, shapes, per, ms / args.steps)
     out = {"metric": "site-updates/s", "value": su * args.steps / (ms * 1e-3), "unit": "site-updates/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
@@ -545,6 +547,49 @@ def run_other(args):
            "gpu_launches": B.gpe_launch_count() - l0, "status": b.sync_status(), **extra}
     print(json.dumps(out), flush=True)
     b.close()
+
+
+def fill_count(shape):
+    """Trajectories of one shape that fill the GPU: at least 2.5e6 sites for 1D grids (every
+    SM holds resident blocks) and 1.6e7 sites for 2D grids (passes of many full waves)."""
+    sites = int(np.prod(shape))
+    target = 2_500_000 if len(shape) == 1 else 16_000_000
+    return max(1, -(-target // sites))
+
+
+def ragged_scheduling_bound(B, shapes, per, measured_ms):
+    """How far the concurrent per-shape streams are from perfect packing.  Each shape of the
+    mix runs alone with enough trajectories to fill the GPU; its rate there (site-updates/s)
+    is the best any schedule of the mix can give its work, so the sum over shapes of
+    work / full-GPU rate bounds from below the time of one step interval -- for the concurrent
+    streams used here or for a single persistent kernel walking all shapes' work."""
+    from collections import Counter
+    per_shape = []
+    ideal_s = 0.0
+    for sh, cnt in sorted(Counter(shapes).items(), key=lambda kv: (len(kv[0]), kv[0])):
+        nf = fill_count(sh)
+        bb = B.GPEBatch(sh, nf, "c64", 1.0, -0.1, 0.09, 0.02)
+        bb.init_noise(W.SEED_BASE, (0.0, 0.0, 1.0, 0.0, 0.0, 0.0), 0.5)
+        bb.step(per)            # warm-up (and tile tuning)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record()
+        for _ in range(reps):
+            bb.step(per)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3 / reps
+        bb.close()
+        sites = int(np.prod(sh))
+        rate = sites * 3 * per * nf / t
+        work = sites * 3 * per * cnt
+        ideal_s += work / rate
+        per_shape.append({"shape": list(sh), "in_mix": cnt, "fill_trajectories": nf, "full_gpu_su_per_s": rate,
+                          "ideal_ms": work / rate * 1e3})
+    return {"measured_ms_per_step": measured_ms, "ideal_ms_per_step": ideal_s * 1e3,
+            "packing_efficiency": ideal_s * 1e3 / measured_ms, "per_shape": per_shape,
+            "note": "ideal = sum over shapes of (the mix's work of that shape / its full-GPU rate)"}
 
 
 def run_adjoint(args):

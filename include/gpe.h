@@ -48,9 +48,10 @@ typedef enum { GPE_C64 = 0, GPE_C128 = 1 } gpe_dtype;
 
 /* One trajectory.  ndim in {1,2,3}; n[a] = points along axis a (x = 0), each a power
  * of two in [64, 1024] for ndim >= 2 and in [64, 32768] (C64) / [64, 16384] (C128) for
- * ndim = 1 (beyond 4096 / 2048 points a 1D trajectory runs on a thread-block cluster;
- * observables support 1D extents up to 4096); unused axes must be 1.  dx = lattice spacing (all axes).  psi = device
- * pointer to the [3][n2][n1][n0] field (caller-owned, 16-byte aligned). */
+ * ndim = 1 (beyond 4096 / 2048 points a 1D trajectory runs on a thread-block cluster,
+ * and its spectra take a four-step transform); unused axes must be 1.  dx = lattice
+ * spacing (all axes).  psi = device pointer to the [3][n2][n1][n0] field (caller-owned,
+ * 16-byte aligned). */
 typedef struct {
     int32_t ndim;
     int32_t n[3];
@@ -125,9 +126,8 @@ gpe_status gpe_step_batch(gpe_batch* batch, int64_t nsteps, void* stream);
  * on a batch allocates the handle's spectra workspace (four fields per trajectory, in
  * chunks of at most 1 GiB); make it before capturing a stream.
  * Errors: GPE_EINVAL (NULL acc, sample_slot < 0, unknown flags), GPE_EUNSUPPORTED
- * (spectra requested for a batch with more than one shape or unequal sides; spectra or
- * diagnostics for x extents above 4096; the winding number for a batch with 2D or 3D
- * trajectories).  The winding number alone allocates no workspace. */
+ * (spectra requested for a batch with more than one shape or unequal sides; the winding
+ * number for a batch with 2D or 3D trajectories).  The winding number alone allocates no workspace. */
 gpe_status observables_accumulate(gpe_batch* batch, double* acc, uint32_t flags,
                                   int32_t sample_slot, void* stream);
 
@@ -197,13 +197,14 @@ gpe_status gpe_batch_set_wait_limit(gpe_batch* batch, int64_t first_wait_polls);
  * Always returns GPE_OK. */
 gpe_status gpe_debug_fail_alloc(int64_t after);
 
-/* Tile autotuner of the strided (y, z) kinetic passes (the paper prescribes none; the
- * choice changes no result bit).  Enabled by default: the first gpe_step_batch call of an
- * FP32 batch times, per shape group with back-to-back fields, every tile width (complex
- * columns per block) the pass is built for on a zero-filled scratch batch of the group's
- * shape (at most 256 MiB, freed again; if it cannot be allocated the defaults stay) and
- * keeps the fastest per axis.  Skipped while the stream is being captured.  Disabled, or
- * for FP64 and non-contiguous groups, fixed per-size defaults are used. */
+/* Tile autotuner of the kinetic passes (the paper prescribes none; the choices change no
+ * result bit).  Enabled by default: the first gpe_step_batch call of an FP32 batch times,
+ * per 2D/3D shape group, on a zero-filled scratch batch of the group's shape (at most
+ * 256 MiB, freed again; if it cannot be allocated the defaults stay), every block size the
+ * x pass is built for and, for groups with back-to-back fields, every tile width (complex
+ * columns per block) the strided passes are built for, and keeps the fastest of each.
+ * Skipped while the stream is being captured.  Disabled, or for FP64 and non-contiguous
+ * groups, fixed per-size defaults are used. */
 gpe_status gpe_batch_set_autotune(gpe_batch* batch, int32_t enable);
 
 /* Fixes the tile widths of the strided passes for trajectory traj's group (and so for
@@ -219,6 +220,16 @@ gpe_status gpe_batch_set_tiles(gpe_batch* batch, int32_t traj, int32_t cols_y, i
  * group has no such pass or uses the non-tensor-map pass), *tuned = 1 once the autotuner
  * has run for the group (tuned may be NULL).  Errors: GPE_EINVAL. */
 gpe_status gpe_batch_get_tiles(const gpe_batch* batch, int32_t traj, int32_t cols[2], int32_t* tuned);
+
+/* Block size of the x pass (local step fused with the x kinetic pass) for trajectory
+ * traj's group.  FP32 2D/3D groups run it with 128 or 256 threads (the autotuner times
+ * both on the first step and keeps the faster; every row goes through the same arithmetic,
+ * so the choice changes no result bit).  set: 128 or 256 fixes it (the autotuner then
+ * leaves it), 0 restores the default; drops the batch's captured graphs.  Errors:
+ * GPE_EINVAL (bad batch, trajectory or size), GPE_EUNSUPPORTED (FP64 batches, 1D groups). */
+gpe_status gpe_batch_set_xpass_threads(gpe_batch* batch, int32_t traj, int32_t threads);
+/* get: the block size in use (0 for 1D groups, which have no x pass).  Errors: GPE_EINVAL. */
+gpe_status gpe_batch_get_xpass_threads(const gpe_batch* batch, int32_t traj, int32_t* threads);
 
 /* Batch time as a step count (t = step * dt); settable for replaying segments. */
 int64_t gpe_batch_get_step(const gpe_batch* batch);

@@ -70,6 +70,8 @@ def _load():
         "gpe_batch_set_autotune": ([vp, i32], ctypes.c_int),
         "gpe_batch_get_tiles": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
         "gpe_batch_set_tiles": ([vp, i32, i32, i32], ctypes.c_int),
+        "gpe_batch_set_xpass_threads": ([vp, i32, i32], ctypes.c_int),
+        "gpe_batch_get_xpass_threads": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "gpe_batch_set_mean_field": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_fma_rate": ([i32, i64, ctypes.POINTER(dbl), vp], ctypes.c_int),
@@ -345,6 +347,16 @@ class GPEBatch:
     def set_tiles(self, cols_y, cols_z=0, traj=0):
         """Fix the strided passes' tile widths of trajectory traj's shape group (0 keeps one)."""
         _check(LIB.gpe_batch_set_tiles(self.h, int(traj), int(cols_y), int(cols_z)))
+
+    def set_xpass_threads(self, threads, traj=0):
+        """Fix the x-pass block size (128 or 256; 0 = default) of trajectory traj's group."""
+        _check(LIB.gpe_batch_set_xpass_threads(self.h, int(traj), int(threads)))
+
+    def xpass_threads(self, traj=0):
+        """Block size of the x pass in use for trajectory traj's group (0 for 1D)."""
+        t = ctypes.c_int32()
+        _check(LIB.gpe_batch_get_xpass_threads(self.h, int(traj), ctypes.byref(t)))
+        return int(t.value)
 
     def tiles(self, traj=0):
         """(cols_y, cols_z, tuned) of the column passes of trajectory traj's group."""

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "adjoint.h"
 #include "gpe.h"
@@ -178,7 +179,13 @@ struct gpe_batch {
 
 namespace {
 
-// Brackets one launch (or launch sequence) of class ``kind`` with events when profiling.
+// NVTX range names of the kernel classes (host-side ranges around each launch sequence,
+// for timeline tools; they cost a pointer test when no tool is attached).
+constexpr const char* kNvtxNames[kProfKinds] = {"gpe.xpass", "gpe.strided_pass", "gpe.resident1d",
+                                                "gpe.noise", "gpe.observables", "gpe.adjoint"};
+
+// Brackets one launch (or launch sequence) of class ``kind`` with an NVTX range and, when
+// profiling, with events.
 struct ProfScope {
     gpe_batch* b;
     int kind;
@@ -186,6 +193,7 @@ struct ProfScope {
     cudaEvent_t e1 = nullptr;
     ProfScope(gpe_batch* b_, int kind_, cudaStream_t s_, int64_t nlaunch) : b(b_), kind(kind_), s(s_) {
         g_launches += nlaunch;
+        nvtxRangePushA(kNvtxNames[kind]);
         if (b->prof.on) {
             cudaEvent_t e0 = b->prof.get();
             e1 = b->prof.get();
@@ -195,6 +203,7 @@ struct ProfScope {
     }
     ~ProfScope() {
         if (e1) cudaEventRecord(e1, s);
+        nvtxRangePop();
     }
 };
 
@@ -406,7 +415,7 @@ cudaError_t x_pass(gpe_batch* b, const Group& g, bool pre, bool half_post, doubl
     a.total_rows = a.rows_per_traj * g.ntraj;
     a.coef.q = (T)q;
     a.vpot = reinterpret_cast<const T*>(g.vpot);
-    return launch_xpass<T>(g.n[0], pre, a, s);
+    return launch_xpass<T>(g.n[0], pre, a, s, g.xthreads);
 }
 
 template <typename T>
@@ -458,13 +467,68 @@ void drop_graphs(gpe_batch* b) {
     b->graphs.clear();
 }
 
-// Column-pass tile autotuner.  On the first step of an FP32 batch, every contiguous shape
-// group times each tile width the column pass is built for (colpass_tma_candidates) on a
-// scratch batch shaped like its own fields -- up to 256 MiB, zero-filled: the pass's cost
-// does not depend on the values -- one warm-up and three timed launches per candidate on
-// the caller's stream, keeps the fastest per axis, frees the scratch and re-encodes the
-// group's tensor maps.  The width changes no result bit.  Skipped while the stream is
-// being captured (the defaults stay) or when disabled.
+// Block size of the x pass that the library uses for group g when none is fixed.
+int xpass_default_threads(const Group& g) { return (g.n[0] == 128 || g.n[0] == 1024) ? 128 : 256; }
+
+// Times the x pass (no leading half kick) on nt scratch fields for each block size it is
+// built for and returns the fastest (0 if nothing could be timed).
+int tune_xpass_threads(gpe_batch* b, const Group& g, void* scratch, int nt, cudaEvent_t e0, cudaEvent_t e1,
+                       cudaStream_t s) {
+    int cand[4];
+    const int nc = xpass_thread_candidates<float>(g.n[0], cand);
+    if (nc == 0) return 0;
+    void** tab = nullptr;
+    if (device_malloc((void**)&tab, sizeof(void*) * nt) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::vector<void*> hp(nt);
+    for (int i = 0; i < nt; ++i) hp[i] = (char*)scratch + (size_t)i * 3 * g.sites * sizeof(float2);
+    int best_t = 0;
+    float best = 0.f;
+    if (cudaMemcpyAsync(tab, hp.data(), sizeof(void*) * nt, cudaMemcpyHostToDevice, s) == cudaSuccess) {
+        PassArgs<float> a = base_args<float>(b, g);
+        a.ptrs = reinterpret_cast<float2* const*>(tab);
+        a.ntraj = nt;
+        for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<float>*>(g.tw[0][ri]);
+        a.ph_pre = reinterpret_cast<const twel<float>*>(g.ph_half[0]);
+        a.ph = reinterpret_cast<const twel<float>*>(g.ph_full[0]);
+        a.rows_per_traj = (int64_t)g.n[1] * g.n[2];
+        a.total_rows = a.rows_per_traj * nt;
+        a.vpot = nullptr;
+        for (int i = 0; i < nc; ++i) {
+            if (launch_xpass<float>(g.n[0], false, a, s, cand[i]) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r) launch_xpass<float>(g.n[0], false, a, s, cand[i]);
+            cudaEventRecord(e1, s);
+            g_launches += 4;
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (best == 0.f || ms < best) {
+                best = ms;
+                best_t = cand[i];
+            }
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(tab);
+    return best_t;
+}
+
+// Tile autotuner.  On the first step of an FP32 batch, every 2D/3D shape group times, on a
+// scratch batch shaped like its own fields -- up to 256 MiB, zero-filled: the passes' cost
+// does not depend on the values -- each block size the x pass is built for and, for groups
+// with back-to-back fields, each tile width the column pass is built for
+// (colpass_tma_candidates), one warm-up and three timed launches per candidate on the
+// caller's stream; it keeps the fastest, frees the scratch and re-encodes the group's tensor
+// maps.  Neither choice changes a result bit.  Skipped while the stream is being captured
+// (the defaults stay) or when disabled; sizes the caller fixed stay.
 gpe_status tune_tiles(gpe_batch* b, cudaStream_t s) {
     if (!b->autotune || b->dtype != GPE_C64) return GPE_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -474,7 +538,7 @@ gpe_status tune_tiles(gpe_batch* b, cudaStream_t s) {
     }
     if (cs != cudaStreamCaptureStatusNone) return GPE_OK;
     for (Group& g : b->groups) {
-        if (g.tuned || g.fixed || !g.contiguous || g.ndim < 2) continue;
+        if (g.tuned || g.ndim < 2 || ((g.fixed || !g.contiguous) && g.xfixed)) continue;
         g.tuned = true;
         const size_t per_traj = (size_t)3 * g.sites * sizeof(float2);
         const size_t cap = ((size_t)256 << 20) / per_traj;
@@ -487,7 +551,12 @@ gpe_status tune_tiles(gpe_batch* b, cudaStream_t s) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         bool ok = cudaMemsetAsync(scratch, 0, per_traj * nt, s) == cudaSuccess &&
                   cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
-        for (int ax = 1; ok && ax < g.ndim; ++ax) {
+        if (ok && !g.xfixed) {
+            const int t = tune_xpass_threads(b, g, scratch, nt, e0, e1, s);
+            if (t > 0) g.xthreads = t;
+        }
+        const bool tune_cols = !g.fixed && g.contiguous;
+        for (int ax = 1; ok && tune_cols && ax < g.ndim; ++ax) {
             int cand[8];
             const int nc = colpass_tma_candidates<float>(g.n[ax], cand);
             float best = 0.f;
@@ -532,7 +601,7 @@ gpe_status tune_tiles(gpe_batch* b, cudaStream_t s) {
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         cudaFree(scratch);
-        if (!encode_group_maps(g, 4)) return fail(GPE_ECUDA, "tensor maps after tile tuning");
+        if (tune_cols && !encode_group_maps(g, 4)) return fail(GPE_ECUDA, "tensor maps after tile tuning");
     }
     return GPE_OK;
 }
@@ -1076,6 +1145,38 @@ gpe_status gpe_batch_set_tiles(gpe_batch* b, int32_t traj, int32_t cols_y, int32
     if (!encode_group_maps(g, 4)) return fail(GPE_ECUDA, "tensor maps for the new tile widths");
     drop_graphs(b);
     return GPE_OK;
+}
+
+gpe_status gpe_batch_set_xpass_threads(gpe_batch* b, int32_t traj, int32_t threads) {
+    g_err.clear();
+    if (!b || traj < 0 || traj >= (int32_t)b->trajs.size()) return fail(GPE_EINVAL, "bad batch or trajectory");
+    Group* gp = nullptr;
+    for (Group& g : b->groups)
+        for (int id : g.ids)
+            if (id == traj) gp = &g;
+    if (!gp) return fail(GPE_EINVAL, "trajectory %d not found", traj);
+    if (b->dtype != GPE_C64 || gp->ndim < 2)
+        return fail(GPE_EUNSUPPORTED, "the x-pass block size is selectable for FP32 2D/3D groups");
+    int cand[4];
+    const int nc = xpass_thread_candidates<float>(gp->n[0], cand);
+    bool built = threads == 0;
+    for (int i = 0; i < nc; ++i) built = built || cand[i] == threads;
+    if (!built) return fail(GPE_EINVAL, "x-pass block size %d is not built", threads);
+    gp->xthreads = threads;
+    gp->xfixed = true;
+    drop_graphs(b);
+    return GPE_OK;
+}
+
+gpe_status gpe_batch_get_xpass_threads(const gpe_batch* b, int32_t traj, int32_t* threads) {
+    if (!b || !threads || traj < 0 || traj >= (int32_t)b->trajs.size()) return fail(GPE_EINVAL, "bad batch or trajectory");
+    for (const Group& g : b->groups)
+        for (int id : g.ids)
+            if (id == traj) {
+                *threads = g.ndim < 2 ? 0 : (g.xthreads > 0 ? g.xthreads : xpass_default_threads(g));
+                return GPE_OK;
+            }
+    return fail(GPE_EINVAL, "trajectory %d not found", traj);
 }
 
 gpe_status gpe_batch_get_tiles(const gpe_batch* b, int32_t traj, int32_t cols[2], int32_t* tuned) {

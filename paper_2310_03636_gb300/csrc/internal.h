@@ -87,6 +87,8 @@ struct Group {
     CUtensorMap map_y{};           // 2D map {2 nx, ntraj 3 nz ny} of the batch (ndim >= 2)
     CUtensorMap map_z{};           // 3D map {2 nx, ny, nz 3 ntraj} (ndim == 3)
     int cols[3] = {0, 0, 0};       // column-pass tile width per axis (1: y, 2: z)
+    int xthreads = 0;              // x-pass block size (0: the default)
+    bool xfixed = false;           // x-pass block size set by the caller (the autotuner leaves it)
     bool tuned = false;            // tile widths chosen by timing
     bool fixed = false;            // tile widths set by the caller (the autotuner skips the group)
     const void* vpot = nullptr;    // caller's potential [3][sites] (real, the batch's precision), or null
@@ -104,8 +106,12 @@ template <typename T> int xpass_max_n();
 template <typename T> int colpass_max_n();
 template <typename T> int resident1d_max_n();
 
+// threads: block size of the x pass (0: the default; FP32 also one of
+// xpass_thread_candidates).
 template <typename T>
-cudaError_t launch_xpass(int n, bool pre, const PassArgs<T>& a, cudaStream_t s);
+cudaError_t launch_xpass(int n, bool pre, const PassArgs<T>& a, cudaStream_t s, int threads = 0);
+template <typename T>
+int xpass_thread_candidates(int n, int* threads);
 template <typename T>
 cudaError_t launch_colpass(int n, const PassArgs<T>& a, cudaStream_t s);
 // Column pass in a given mode: 0 kinetic factor, 1 forward FFT only, 2 adjoint kinetic

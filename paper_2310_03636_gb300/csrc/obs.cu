@@ -4,6 +4,10 @@
 //                   q (n_1 + n_-1), c0 rho^2 / 2, c1 (F_z^2 + |F_perp|^2) / 2 and, with a
 //                   potential, sum_m V_m n_m per site block;
 //   2. forward FFTs of the 4 fields along every axis (same pencil FFT as the propagation);
+//      1D grids longer than one block's transform (N = C M, the thread-block-cluster
+//      sizes) take a four-step transform: k_obs_cross does the length-C DFTs across the C
+//      slices of length M and the twiddles W_N^{n k1}, then length-M row FFTs give mode
+//      k1 + C k2 at position k1 M + k2; the bin tables and k^2 use that order;
 //   3. k_obs_ekin   FP64 partial sums of (k^2/2) |psi_m(k)|^2 per mode block;
 //   4. k_obs_bins   per (radial bin, field): sum over trajectories and the bin's modes of
 //                   |W|^2 dx^d / N (- 1/2 for the occupations), FP64, into the caller's
@@ -18,6 +22,7 @@
 #include <string>
 #include <vector>
 
+#include "fft.cuh"
 #include "obs.h"
 
 namespace gpe {
@@ -120,10 +125,16 @@ k_obs_prep(cplx<T>* const* __restrict__ ptrs, int t0, cplx<T>* __restrict__ W, i
 
 // Kinetic energy partials: sum over a block's modes of (k^2 / 2) |psi_m(k)|^2, mode
 // coordinates from shifts (all extents are powers of two), terms in the fields' precision.
+// Mode number along x of position i of a transformed row: natural order, or with lm > 0
+// the four-step order (position k1 M + k2 holds mode k1 + C k2, M = 2^lm, C = 2^lc).
+__host__ __device__ __forceinline__ int64_t x_mode(int64_t i, int lm, int lc) {
+    return lm > 0 ? (i >> lm) + ((i & ((1ll << lm) - 1)) << lc) : i;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_obs_ekin(const cplx<T>* __restrict__ W, int64_t sites, int lx, int ly, int nz, double dx,
-           double* __restrict__ ekin, int64_t nblk) {
+           double* __restrict__ ekin, int64_t nblk, int lm, int lc) {
     using V = cplx<T>;
     __shared__ double sm[32];
     const int nx = 1 << lx, ny = 1 << ly;
@@ -136,7 +147,7 @@ k_obs_ekin(const cplx<T>* __restrict__ W, int64_t sites, int lx, int ly, int nz,
     for (int k = 0; k < kSitesPerBlock / kThreads; ++k) {
         const int64_t i = s0 + k * kThreads + threadIdx.x;
         if (i >= sites) break;
-        const int ix = (int)(i & (nx - 1));
+        const int ix = (int)(x_mode(i & (nx - 1), lm, lc));
         const int iy = (int)((i >> lx) & (ny - 1));
         const int iz = (int)(i >> (lx + ly));
         const T kx = gx * (T)fold(ix, nx), ky = gy * (T)fold(iy, ny), kz = gz * (T)fold(iz, nz);
@@ -201,6 +212,41 @@ k_obs_final(const double* __restrict__ part, const double* __restrict__ ekin, in
     }
 }
 
+// First step of the four-step transform of rows of N = C M points: row element n1 M + n2
+// (n1 < C, n2 < M) is replaced by W_N^{n2 k1} sum_{n1} x[n1 M + n2] W_C^{n1 k1} at k1 M + n2,
+// so that length-M transforms of the C slices give X[k1 + C k2] at k1 M + k2.  One thread
+// per (row, n2); wn[k1 M + n2] = W_N^{n2 k1}.
+template <typename T, int C>
+__global__ void __launch_bounds__(kThreads)
+k_obs_cross(cplx<T>* __restrict__ W, int64_t rows, int M, const twel<T>* __restrict__ wn) {
+    using V = cplx<T>;
+    const int64_t gid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (gid >= rows * M) return;
+    const int64_t row = gid / M;
+    const int n2 = (int)(gid - row * M);
+    V* r = W + row * (int64_t)C * M + n2;
+    V x[C];
+#pragma unroll
+    for (int n1 = 0; n1 < C; ++n1) x[n1] = r[(int64_t)n1 * M];
+    Dft<C, 1, -1>::run(x);
+    r[0] = x[0];
+#pragma unroll
+    for (int k1 = 1; k1 < C; ++k1) r[(int64_t)k1 * M] = twmul<-1>(x[k1], wn[(int64_t)k1 * M + n2]);
+}
+
+template <typename T>
+cudaError_t launch_obs_cross(int C, cplx<T>* W, int64_t rows, int M, const twel<T>* wn, cudaStream_t s) {
+    const int64_t total = rows * M;
+    const unsigned grid = (unsigned)((total + kThreads - 1) / kThreads);
+    switch (C) {
+        case 2: k_obs_cross<T, 2><<<grid, kThreads, 0, s>>>(W, rows, M, wn); break;
+        case 4: k_obs_cross<T, 4><<<grid, kThreads, 0, s>>>(W, rows, M, wn); break;
+        case 8: k_obs_cross<T, 8><<<grid, kThreads, 0, s>>>(W, rows, M, wn); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // Winding number of the Larmor angle phi_L = arg(F_perp) around a periodic 1D trajectory
 // (Sec. 1: Q_w = int dx d_x phi_L), in units of 2 pi: the sum over x of the increments
 // arg(F(x)^* F(x+1)) in (-pi, pi], FP64, fixed summation order.  One block per trajectory.
@@ -254,10 +300,20 @@ gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q,
             w.d_part, w.nblk);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs prep", e);
-        const twel<T>* twx[3] = {reinterpret_cast<const twel<T>*>(g.tw[0][0]),
-                                 reinterpret_cast<const twel<T>*>(g.tw[0][1]),
-                                 reinterpret_cast<const twel<T>*>(g.tw[0][2])};
-        e = launch_rowfft<T>(g.n[0], W, (int64_t)nc * 4 * g.n[1] * g.n[2], twx, s);
+        if (g.cluster > 0) {
+            // 1D N = C M: cross step, then length-M row transforms of the C slices
+            const int M = g.n[0] / g.cluster;
+            const twel<T>* twl[3] = {reinterpret_cast<const twel<T>*>(g.tw_local[0]),
+                                     reinterpret_cast<const twel<T>*>(g.tw_local[1]),
+                                     reinterpret_cast<const twel<T>*>(g.tw_local[2])};
+            e = launch_obs_cross<T>(g.cluster, W, (int64_t)nc * 4, M, reinterpret_cast<const twel<T>*>(g.wn), s);
+            if (e == cudaSuccess) e = launch_rowfft<T>(M, W, (int64_t)nc * 4 * g.cluster, twl, s);
+        } else {
+            const twel<T>* twx[3] = {reinterpret_cast<const twel<T>*>(g.tw[0][0]),
+                                     reinterpret_cast<const twel<T>*>(g.tw[0][1]),
+                                     reinterpret_cast<const twel<T>*>(g.tw[0][2])};
+            e = launch_rowfft<T>(g.n[0], W, (int64_t)nc * 4 * g.n[1] * g.n[2], twx, s);
+        }
         if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs x fft", e);
         for (int ax = 1; ax < g.ndim; ++ax) {
             PassArgs<T> a{};
@@ -282,11 +338,15 @@ gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q,
             if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs strided fft", e);
         }
         if (flags & GPE_OBS_DIAG) {
-            int lx = 0, ly = 0;
+            int lx = 0, ly = 0, lm = 0, lc = 0;
             while ((1 << lx) < g.n[0]) ++lx;
             while ((1 << ly) < g.n[1]) ++ly;
+            if (g.cluster > 0) {
+                while ((1 << lc) < g.cluster) ++lc;
+                lm = lx - lc;
+            }
             k_obs_ekin<T><<<dim3((unsigned)nblk, 3, nc), kThreads, 0, s>>>(W, g.sites, lx, ly, g.n[2], g.dx,
-                                                                          w.d_ekin, w.nblk);
+                                                                          w.d_ekin, w.nblk, lm, lc);
             k_obs_final<<<nc, kThreads, 0, s>>>(w.d_part, w.d_ekin, w.nblk, nblk, g.d_ids, t0, vol, 1.0 / (double)g.sites,
                                                 acc_slot + 4 * (int64_t)(w.nbins > 0 ? w.nbins : 0), d_status);
             e = cudaGetLastError();
@@ -323,7 +383,8 @@ int64_t obs_launches(const ObsWork& w, const std::vector<Group>& groups, uint32_
         const int64_t c = chunk > 0 ? chunk : max_traj;  // before the first call: estimate
         const int64_t nchunks = (g.ntraj + c - 1) / c;
         const bool fields = flags & (GPE_OBS_SPECTRA | GPE_OBS_DIAG);
-        const int64_t per = (fields ? 1 + g.ndim : 0) + ((flags & GPE_OBS_DIAG) ? 2 : 0) + ((flags & GPE_OBS_SPECTRA) ? 1 : 0);
+        const int64_t per = (fields ? 1 + g.ndim + (g.cluster > 0 ? 1 : 0) : 0) + ((flags & GPE_OBS_DIAG) ? 2 : 0) +
+                            ((flags & GPE_OBS_SPECTRA) ? 1 : 0);
         n += nchunks * per + ((flags & GPE_OBS_WINDING) ? 1 : 0);
     }
     return n;
@@ -340,10 +401,15 @@ gpe_status obs_init(ObsWork& w, const std::vector<Group>& groups, bool f64, int)
         if (g.n[a] != g.n[0]) return GPE_OK;
     const int n = g.n[0];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    int lm = 0, lc = 0;   // four-step order of 1D cluster groups (see k_obs_cross)
+    if (g.cluster > 0) {
+        while ((1 << lc) < g.cluster) ++lc;
+        while ((1 << lm) < nx / g.cluster) ++lm;
+    }
     std::vector<int32_t> bin(g.sites);
     int64_t maxb = 0;
     for (int64_t i = 0; i < g.sites; ++i) {
-        const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((int64_t)nx * ny));
+        const int ix = (int)x_mode(i % nx, lm, lc), iy = (int)((i / nx) % ny), iz = (int)(i / ((int64_t)nx * ny));
         const int64_t jx = fold(ix, nx), jy = fold(iy, ny), jz = fold(iz, nz);
         const int64_t b = isqrt_round(jx * jx + jy * jy + jz * jz);
         bin[i] = (int32_t)b;
@@ -422,8 +488,8 @@ gpe_status obs_accumulate(ObsWork& w, const std::vector<Group>& groups, bool f64
                           double* acc, uint32_t flags, int slot, int* d_status, cudaStream_t s) {
     const bool fields = flags & (GPE_OBS_SPECTRA | GPE_OBS_DIAG);
     for (const Group& g : groups) {
-        if (fields && g.n[0] > 4096) {
-            g_obs_err = "spectra and diagnostics support x extents up to 4096";
+        if (fields && g.n[0] > 4096 && g.cluster == 0) {
+            g_obs_err = "spectra and diagnostics support x extents up to 4096 (longer 1D grids take the cluster path)";
             return GPE_EUNSUPPORTED;
         }
         if ((flags & GPE_OBS_WINDING) && g.ndim != 1) {

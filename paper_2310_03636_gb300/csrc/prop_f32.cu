@@ -7,16 +7,32 @@ template <> int xpass_max_n<float>() { return 1024; }
 template <> int colpass_max_n<float>() { return 1024; }
 template <> int colpass_cols<float>(int n) { return Tune<float>::kColCols(n); }
 
-template <>
-cudaError_t launch_xpass<float>(int n, bool pre, const PassArgs<float>& a, cudaStream_t s) {
-    switch (n) {
-        case 64: return xpass_n<float, 64>(pre, a, s);
-        case 128: return xpass_n<float, 128>(pre, a, s);
-        case 256: return xpass_n<float, 256>(pre, a, s);
-        case 512: return xpass_n<float, 512>(pre, a, s);
-        case 1024: return xpass_n<float, 1024>(pre, a, s);
+template <int NN>
+static cudaError_t xpass_threads(int threads, bool pre, const PassArgs<float>& a, cudaStream_t s) {
+    switch (threads) {
+        case 0: return xpass_n<float, NN>(pre, a, s);
+        case 128: return xpass_n<float, NN, 128>(pre, a, s);
+        case 256: return xpass_n<float, NN, 256>(pre, a, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <>
+cudaError_t launch_xpass<float>(int n, bool pre, const PassArgs<float>& a, cudaStream_t s, int threads) {
+    switch (n) {
+        case 64: return xpass_threads<64>(threads, pre, a, s);
+        case 128: return xpass_threads<128>(threads, pre, a, s);
+        case 256: return xpass_threads<256>(threads, pre, a, s);
+        case 512: return xpass_threads<512>(threads, pre, a, s);
+        case 1024: return xpass_threads<1024>(threads, pre, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+int xpass_thread_candidates<float>(int, int* threads) {
+    for (int i = 0; i < 2; ++i) threads[i] = kXpassThreads[i];
+    return 2;
 }
 
 template <>

@@ -4,11 +4,13 @@
 namespace gpe {
 
 template <> int xpass_max_n<double>() { return 1024; }
+template <> int xpass_thread_candidates<double>(int, int*) { return 0; }
 template <> int colpass_max_n<double>() { return 1024; }
 template <> int colpass_cols<double>(int n) { return Tune<double>::kColCols(n); }
 
 template <>
-cudaError_t launch_xpass<double>(int n, bool pre, const PassArgs<double>& a, cudaStream_t s) {
+cudaError_t launch_xpass<double>(int n, bool pre, const PassArgs<double>& a, cudaStream_t s, int threads) {
+    if (threads != 0) return cudaErrorInvalidValue;   // FP64: the default block size only
     switch (n) {
         case 64: return xpass_n<double, 64>(pre, a, s);
         case 128: return xpass_n<double, 128>(pre, a, s);

@@ -45,11 +45,13 @@ constexpr int smem_ld_cols(int n, int cols) {
 
 template <int N, int R> constexpr int rows_per_cta() { return (N / R) >= 256 ? 1 : 256 / (N / R); }
 
-// Rows per block of the x pass: 256 threads, except 128 at n = 128 and n = 1024 (measured:
-// 196 vs 207 us at 128^2 x 512, 459 vs 474 us at 1024^2 x 16; 256 threads are faster at 256
-// and 512).
-template <int N, int R> constexpr int xpass_rows() {
-    const int threads = (N == 128 || N == 1024) ? 128 : 256;
+// Rows per block of the x pass for a block of THREADS threads; THREADS = 0 is the default,
+// 256 threads except 128 at n = 128 and n = 1024 (measured: 196 vs 207 us at 128^2 x 512,
+// 459 vs 474 us at 1024^2 x 16; 256 threads are faster at 256 and 512).  The FP32 tile
+// autotuner may pick the other size per shape: every row goes through the same arithmetic
+// either way, so the choice changes no result bit.
+template <int N, int R, int THREADS = 0> constexpr int xpass_rows() {
+    const int threads = THREADS > 0 ? THREADS : ((N == 128 || N == 1024) ? 128 : 256);
     return (N / R) >= threads ? 1 : threads / (N / R);
 }
 
@@ -87,12 +89,12 @@ __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const t
 // Row pass over RPC x rows of all three components: bulk copies bring the rows into
 // shared memory, then [PRE: Kx(dt/2)] L(dt) per site, Kx(tau) per component, and bulk
 // copies write them back.
-template <typename T, int N, int R, bool PRE>
-__global__ void __launch_bounds__(xpass_rows<N, R>() * (N / R))
+template <typename T, int N, int R, bool PRE, int THREADS = 0>
+__global__ void __launch_bounds__(xpass_rows<N, R, THREADS>() * (N / R))
 k_xpass(const PassArgs<T> a) {
     using V = cplx<T>;
     constexpr int TP = N / R;
-    constexpr int RPC = xpass_rows<N, R>();
+    constexpr int RPC = xpass_rows<N, R, THREADS>();
     constexpr int LD = smem_ld<T>(N);
     constexpr int TWN = FftPlan<N, R>::tw_size();
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -189,9 +191,10 @@ k_xpass(const PassArgs<T> a) {
     }
 }
 
-template <typename T, int N, int R>
+template <typename T, int N, int R, int THREADS = 0>
 constexpr size_t xpass_smem() {
-    return ((size_t)xpass_rows<N, R>() * 3 * N + tw_off<T>(xpass_rows<N, R>() * smem_ld<T>(N))) * sizeof(cplx<T>) +
+    return ((size_t)xpass_rows<N, R, THREADS>() * 3 * N + tw_off<T>(xpass_rows<N, R, THREADS>() * smem_ld<T>(N))) *
+               sizeof(cplx<T>) +
            FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
 }
 
@@ -431,16 +434,19 @@ inline cudaError_t launch_with_smem(K kernel, int grid, int block, size_t smem, 
     return cudaLaunchKernel((const void*)kernel, dim3(grid), dim3(block), args, smem, s);
 }
 
-template <typename T, int N>
+template <typename T, int N, int THREADS = 0>
 cudaError_t xpass_n(bool pre, const PassArgs<T>& a, cudaStream_t s) {
     constexpr int R = Tune<T>::kXR;
     constexpr int TP = N / R;
-    constexpr int RPC = xpass_rows<N, R>();
+    constexpr int RPC = xpass_rows<N, R, THREADS>();
     const int64_t grid = (a.total_rows + RPC - 1) / RPC;
-    const size_t smem = xpass_smem<T, N, R>();
-    if (pre) return launch_with_smem(k_xpass<T, N, R, true>, (int)grid, RPC * TP, smem, s, &a);
-    return launch_with_smem(k_xpass<T, N, R, false>, (int)grid, RPC * TP, smem, s, &a);
+    const size_t smem = xpass_smem<T, N, R, THREADS>();
+    if (pre) return launch_with_smem(k_xpass<T, N, R, true, THREADS>, (int)grid, RPC * TP, smem, s, &a);
+    return launch_with_smem(k_xpass<T, N, R, false, THREADS>, (int)grid, RPC * TP, smem, s, &a);
 }
+
+// Block sizes the FP32 x pass is built for (the tuner's candidates); 0 = the default.
+constexpr int kXpassThreads[2] = {128, 256};
 
 template <typename T, int N, int MODE>
 cudaError_t colpass_n(const PassArgs<T>& a, cudaStream_t s) {

@@ -205,6 +205,11 @@ def oracle_observables(psi, dx, d, q=Q):
     ("c128", (128, 128), 3, 0.8, 30),
     ("c64", (128, 128), 4, 1.0, 30),
     ("c128", (64, 64, 64), 2, 1.0, 5),
+    # 1D grids on thread-block clusters: spectra through the four-step transform
+    ("c128", (4096,), 2, 1.0, 20),          # FP64 cluster of 2 x 2048
+    ("c128", (16384,), 1, 0.7, 10),         # FP64 cluster of 8 x 2048
+    ("c64", (8192,), 2, 1.0, 20),           # FP32 cluster of 2 x 4096
+    ("c64", (32768,), 2, 1.0, 10),          # FP32 cluster of 8 x 4096
 ])
 def test_observables(B, dtype, shape, ntraj, dx, steps):
     b = B.GPEBatch(shape, ntraj, dtype, C0, C1, Q, 0.02, dx=dx)
@@ -524,6 +529,34 @@ def test_autotuned_tiles_change_no_bit(B, shape, ntraj):
         cy, cz, tuned = b.tiles(0)
         assert tuned == tune
         assert cy in (2, 4, 8, 16) and (cz in (2, 4, 8, 16) if len(shape) == 3 else cz == 0)
+        assert b.xpass_threads(0) in (128, 256)
         out.append(b.psi.cpu().numpy())
         b.close()
     np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("shape,ntraj", [((64, 64), 3), ((128, 128), 2), ((256, 64, 128), 2), ((1024, 512), 1),
+                                         ((512, 1024), 1)])
+def test_every_xpass_block_size_gives_the_same_bits(B, shape, ntraj):
+    """Both x-pass block sizes (fixed through gpe_batch_set_xpass_threads; rows per block
+    change, the per-row arithmetic does not) give the same fields bit for bit; sizes that are
+    not built and FP64 batches are refused."""
+    out = []
+    for th in (128, 256):
+        b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, 0.02)
+        b.set_autotune(False)
+        b.set_xpass_threads(th)
+        assert b.xpass_threads(0) == th
+        b.init_noise(9, MEAN, 0.5)
+        b.step(5)
+        assert b.sync_status() == B.GPE_OK
+        out.append(b.psi.cpu().numpy())
+        with pytest.raises(B.GPEError):
+            b.set_xpass_threads(192)
+        b.close()
+    np.testing.assert_array_equal(out[0], out[1])
+    b = B.GPEBatch(shape, 1, "c128")
+    with pytest.raises(B.GPEError) as ei:
+        b.set_xpass_threads(128)
+    assert ei.value.status == B.GPE_EUNSUPPORTED
+    b.close()
