@@ -161,7 +161,7 @@ class Clocks:
 # Sources that define the propagation passes (x pass and strided passes); the ncu traffic
 # figures in profiles/ stay valid while these are unchanged.
 PASS_SOURCES = ("common.cuh", "fft.cuh", "local_step.cuh", "async_copy.cuh", "prop_kernels.cuh", "prop_f32.cu",
-                "prop_f64.cu", "colpass_tma_f32.cu", "internal.h")
+                "prop_f64.cu", "colpass_tma_f32.cu", "xpass_f32_small.cu", "xpass_f32_large.cu", "internal.h")
 
 
 def kernel_source_hash():

@@ -285,6 +285,19 @@ gpe_status dev_alloc(gpe_batch* b, void** p, size_t bytes) {
     return GPE_OK;
 }
 
+// Compact form of an FP32 kinetic phase table for the x pass: (p, u) of modes 0..n/2 (the
+// table is symmetric in k), possible when no entry needed a sign (every angle within
+// +-pi/2, so the entry's third value is the common 1/n).  Empty otherwise.
+std::vector<float2> compact_phases(const std::vector<float4>& t) {
+    const int n = (int)t.size();
+    std::vector<float2> c;
+    for (int i = 0; i < n; ++i)
+        if (!(t[i].z > 0.0f) || t[i].z != t[0].z) return c;
+    for (int i = 0; i <= n / 2; ++i) c.push_back(make_float2(t[i].x, t[i].y));
+    return c;
+}
+std::vector<float2> compact_phases(const std::vector<double2>&) { return {}; }
+
 template <typename T>
 gpe_status build_group_tables(gpe_batch* b, Group& g) {
     for (int a = 0; a < g.ndim; ++a) {
@@ -296,6 +309,16 @@ gpe_status build_group_tables(gpe_batch* b, Group& g) {
         if ((s = dev_alloc(b, &g.ph_half[a], bytes)) != GPE_OK) return s;
         GPE_CK(cudaMemcpy(g.ph_full[a], pf.data(), bytes, cudaMemcpyHostToDevice));
         GPE_CK(cudaMemcpy(g.ph_half[a], ph.data(), bytes, cudaMemcpyHostToDevice));
+        if (a == 0 && g.ndim >= 2) {
+            const std::vector<float2> cf = compact_phases(pf), ch = compact_phases(ph);
+            if (!cf.empty() && !ch.empty()) {
+                const size_t cb = sizeof(float2) * cf.size();
+                if ((s = dev_alloc(b, &g.phc_full, cb)) != GPE_OK) return s;
+                if ((s = dev_alloc(b, &g.phc_half, cb)) != GPE_OK) return s;
+                GPE_CK(cudaMemcpy(g.phc_full, cf.data(), cb, cudaMemcpyHostToDevice));
+                GPE_CK(cudaMemcpy(g.phc_half, ch.data(), cb, cudaMemcpyHostToDevice));
+            }
+        }
         for (int ri = 0; ri < 3; ++ri) {
             const std::vector<twel<T>> tw = stage_twiddles_host<T>(g.n[a], 4 << ri);
             const size_t tb = sizeof(twel<T>) * tw.size();
@@ -411,6 +434,11 @@ cudaError_t x_pass(gpe_batch* b, const Group& g, bool pre, bool half_post, doubl
     for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<T>*>(g.tw[0][ri]);
     a.ph_pre = reinterpret_cast<const twel<T>*>(g.ph_half[0]);
     a.ph = reinterpret_cast<const twel<T>*>(half_post ? g.ph_half[0] : g.ph_full[0]);
+    if (g.phc_full) {
+        a.phc = reinterpret_cast<const float2*>(half_post ? g.phc_half : g.phc_full);
+        a.phc_pre = reinterpret_cast<const float2*>(g.phc_half);
+        a.ph_scale = 1.0f / (float)g.n[0];
+    }
     a.rows_per_traj = (int64_t)g.n[1] * g.n[2];
     a.total_rows = a.rows_per_traj * g.ntraj;
     a.coef.q = (T)q;
@@ -476,7 +504,7 @@ int tune_xpass_threads(gpe_batch* b, const Group& g, void* scratch, int nt, cuda
                        cudaStream_t s) {
     int cand[4];
     const int nc = xpass_thread_candidates<float>(g.n[0], cand);
-    if (nc == 0) return 0;
+    if (nc == 0 || !g.phc_full) return 0;   // block sizes are built for the compact-table pass only
     void** tab = nullptr;
     if (device_malloc((void**)&tab, sizeof(void*) * nt) != cudaSuccess) {
         cudaGetLastError();
@@ -493,6 +521,11 @@ int tune_xpass_threads(gpe_batch* b, const Group& g, void* scratch, int nt, cuda
         for (int ri = 0; ri < 3; ++ri) a.tw[ri] = reinterpret_cast<const twel<float>*>(g.tw[0][ri]);
         a.ph_pre = reinterpret_cast<const twel<float>*>(g.ph_half[0]);
         a.ph = reinterpret_cast<const twel<float>*>(g.ph_full[0]);
+        if (g.phc_full) {
+            a.phc = reinterpret_cast<const float2*>(g.phc_full);
+            a.phc_pre = reinterpret_cast<const float2*>(g.phc_half);
+            a.ph_scale = 1.0f / (float)g.n[0];
+        }
         a.rows_per_traj = (int64_t)g.n[1] * g.n[2];
         a.total_rows = a.rows_per_traj * nt;
         a.vpot = nullptr;
@@ -1155,8 +1188,10 @@ gpe_status gpe_batch_set_xpass_threads(gpe_batch* b, int32_t traj, int32_t threa
         for (int id : g.ids)
             if (id == traj) gp = &g;
     if (!gp) return fail(GPE_EINVAL, "trajectory %d not found", traj);
-    if (b->dtype != GPE_C64 || gp->ndim < 2)
-        return fail(GPE_EUNSUPPORTED, "the x-pass block size is selectable for FP32 2D/3D groups");
+    if (b->dtype != GPE_C64 || gp->ndim < 2 || !gp->phc_full)
+        return fail(GPE_EUNSUPPORTED,
+                    "the x-pass block size is selectable for FP32 2D/3D groups whose kinetic angles are within "
+                    "pi/2 (dt < dx^2 / pi)");
     int cand[4];
     const int nc = xpass_thread_candidates<float>(gp->n[0], cand);
     bool built = threads == 0;

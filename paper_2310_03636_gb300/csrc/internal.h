@@ -34,6 +34,12 @@ struct PassArgs {
     const twel<T>* ph;        // phase table exp(-i tau k^2 / 2) / N
     LocalCoef<T> coef;        // couplings for the local step (row pass)
     const T* vpot;            // row pass: potential [3][sites] shared by the group, or null
+    // FP32 row pass, when every kinetic angle of the x tables lies within +-pi/2: the
+    // phase tables as (p, u) of the three-shear rotation for modes 0..N/2 (the table is
+    // symmetric in k), the common factor 1/N apart; null otherwise
+    const float2* phc;        // for ph
+    const float2* phc_pre;    // for ph_pre
+    float ph_scale;           // 1/N
     int* status;              // device status word (bounded waits that expire)
     uint32_t wait_first;      // row pass: 0 = default limit of the first copy wait, else 1 + its poll limit
 };
@@ -80,6 +86,8 @@ struct Group {
     void* tw[3][3] = {};           // per axis: stage twiddle tables for R = 4, 8, 16
     void* ph_full[3] = {};         // per axis: exp(-i dt k^2/2)/n
     void* ph_half[3] = {};         // per axis: exp(-i dt k^2/4)/n
+    void* phc_full = nullptr;      // FP32 x axis: compact (p, u) tables for modes 0..n/2, when
+    void* phc_half = nullptr;      //   every angle is within +-pi/2 (else null)
     bool contiguous = false;       // fields back to back from hptrs[0]: tensor-map passes usable
     int cluster = 0;               // 1D on a thread-block cluster: blocks per trajectory (0: off)
     void* tw_local[3] = {};        // cluster 1D: stage twiddles of the per-block length M
@@ -112,6 +120,9 @@ template <typename T>
 cudaError_t launch_xpass(int n, bool pre, const PassArgs<T>& a, cudaStream_t s, int threads = 0);
 template <typename T>
 int xpass_thread_candidates(int n, int* threads);
+// The FP32 x pass for x extents up to 256 and from 512 (two translation units).
+cudaError_t launch_xpass_f32_small(int n, bool pre, const PassArgs<float>& a, cudaStream_t s, int threads);
+cudaError_t launch_xpass_f32_large(int n, bool pre, const PassArgs<float>& a, cudaStream_t s, int threads);
 template <typename T>
 cudaError_t launch_colpass(int n, const PassArgs<T>& a, cudaStream_t s);
 // Column pass in a given mode: 0 kinetic factor, 1 forward FFT only, 2 adjoint kinetic

@@ -7,26 +7,10 @@ template <> int xpass_max_n<float>() { return 1024; }
 template <> int colpass_max_n<float>() { return 1024; }
 template <> int colpass_cols<float>(int n) { return Tune<float>::kColCols(n); }
 
-template <int NN>
-static cudaError_t xpass_threads(int threads, bool pre, const PassArgs<float>& a, cudaStream_t s) {
-    switch (threads) {
-        case 0: return xpass_n<float, NN>(pre, a, s);
-        case 128: return xpass_n<float, NN, 128>(pre, a, s);
-        case 256: return xpass_n<float, NN, 256>(pre, a, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 template <>
 cudaError_t launch_xpass<float>(int n, bool pre, const PassArgs<float>& a, cudaStream_t s, int threads) {
-    switch (n) {
-        case 64: return xpass_threads<64>(threads, pre, a, s);
-        case 128: return xpass_threads<128>(threads, pre, a, s);
-        case 256: return xpass_threads<256>(threads, pre, a, s);
-        case 512: return xpass_threads<512>(threads, pre, a, s);
-        case 1024: return xpass_threads<1024>(threads, pre, a, s);
-        default: return cudaErrorInvalidValue;
-    }
+    if (n <= 256) return launch_xpass_f32_small(n, pre, a, s, threads);
+    return launch_xpass_f32_large(n, pre, a, s, threads);
 }
 
 template <>

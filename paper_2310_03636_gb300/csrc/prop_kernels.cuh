@@ -68,9 +68,13 @@ __host__ __device__ constexpr uint32_t first_wait_limit(uint32_t wait_first) {
 // t + m TP), times a phase table, inverse FFT, back into shared memory.  A row of at most
 // 32 threads lies within one warp, so its exchanges synchronise the warp only; the rows
 // of a block with several larger rows synchronise with a barrier of their own.
-template <typename T, int N, int R, int RPC = 1>
+// With CPH (FP32) the phases come from a compact table in shared memory: (p, u) of the
+// three-shear rotation for modes 0..N/2 (mode k and N - k share an entry) and the common
+// factor scale = 1/N, the same numbers phmul takes from the full table, so the same bits.
+template <typename T, int N, int R, int RPC = 1, bool CPH = false>
 __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const twel<T>* tws,
-                                            const twel<T>* __restrict__ ph, int t) {
+                                            const twel<T>* __restrict__ ph, int t, const float2* phc = nullptr,
+                                            float scale = 0.0f) {
     using V = cplx<T>;
     constexpr int TP = N / R;
     V v[1][R];
@@ -79,8 +83,18 @@ __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const t
     for (int m = 0; m < R; ++m) v[0][m] = row[t + m * TP];
     constexpr Sync SY = TP <= 32 ? Sync::Warp : (RPC > 1 ? Sync::Group : Sync::Block);
     fft_pencil<N, R, -1, 1, SY>(v, xb, tws, t);
+    if constexpr (CPH && sizeof(T) == 4) {
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
+        for (int m = 0; m < R; ++m) {
+            const int k = t + m * TP;
+            const float2 f = phc[k <= N / 2 ? k : N - k];
+            const float2 r = lift_rot(v[0][m], f.x, f.y);
+            v[0][m] = make_float2(r.x * scale, r.y * scale);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
+    }
     fft_pencil<N, R, +1, 1, SY>(v, xb, tws, t);
 #pragma unroll
     for (int m = 0; m < R; ++m) row[t + m * TP] = v[0][m];
@@ -89,7 +103,11 @@ __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const t
 // Row pass over RPC x rows of all three components: bulk copies bring the rows into
 // shared memory, then [PRE: Kx(dt/2)] L(dt) per site, Kx(tau) per component, and bulk
 // copies write them back.
-template <typename T, int N, int R, bool PRE, int THREADS = 0>
+// Compact phase tables the x pass keeps in shared memory (CPH): one, two with the leading
+// half kick.
+template <int N, bool PRE> constexpr int xpass_cph_entries() { return ((PRE ? 2 : 1) * (N / 2 + 1) + 1) & ~1; }
+
+template <typename T, int N, int R, bool PRE, int THREADS = 0, bool CPH = false>
 __global__ void __launch_bounds__(xpass_rows<N, R, THREADS>() * (N / R))
 k_xpass(const PassArgs<T> a) {
     using V = cplx<T>;
@@ -102,6 +120,7 @@ k_xpass(const PassArgs<T> a) {
     V* X = D + RPC * 3 * N;                                      // [RPC][LD] exchange
     twel<T>* tws = reinterpret_cast<twel<T>*>(X + tw_off<T>(RPC * LD));
     uint64_t* bar = reinterpret_cast<uint64_t*>(tws + TWN);
+    float2* phc = reinterpret_cast<float2*>(bar + 2);   // CPH: [ph][ph_pre] compact tables
     const int lrow = threadIdx.x / TP, t = threadIdx.x % TP;
     const int64_t row0 = (int64_t)blockIdx.x * RPC;
     const int nrows = (int)min((int64_t)RPC, a.total_rows - row0);
@@ -119,6 +138,10 @@ k_xpass(const PassArgs<T> a) {
         }
     }
     copy_table(tws, a.tw[tw_slot<R>()], TWN);
+    if constexpr (CPH) {
+        copy_table(phc, a.phc, N / 2 + 1);
+        if constexpr (PRE) copy_table(phc + (N / 2 + 1), a.phc_pre, N / 2 + 1);
+    }
     const bool ok = __syncthreads_and(mbar_wait(bar, 0, first_wait_limit(a.wait_first)));
     if (!ok) {
         if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)GPE_ETIMEOUT);
@@ -129,7 +152,8 @@ k_xpass(const PassArgs<T> a) {
     V* Xr = X + lrow * LD;
     if constexpr (PRE) {
 #pragma unroll 1
-        for (int c = 0; c < 3; ++c) kinetic_row<T, N, R, RPC>(Dr + c * N, Xr, tws, a.ph_pre, t);
+        for (int c = 0; c < 3; ++c)
+            kinetic_row<T, N, R, RPC, CPH>(Dr + c * N, Xr, tws, a.ph_pre, t, phc + (N / 2 + 1), a.ph_scale);
     }
     if (lrow < nrows) {
         if (sizeof(T) == 4 && a.vpot == nullptr && a.coef.kind == 0) {
@@ -175,7 +199,7 @@ k_xpass(const PassArgs<T> a) {
         }
     }
 #pragma unroll 1
-    for (int c = 0; c < 3; ++c) kinetic_row<T, N, R, RPC>(Dr + c * N, Xr, tws, a.ph, t);
+    for (int c = 0; c < 3; ++c) kinetic_row<T, N, R, RPC, CPH>(Dr + c * N, Xr, tws, a.ph, t, phc, a.ph_scale);
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -191,11 +215,12 @@ k_xpass(const PassArgs<T> a) {
     }
 }
 
-template <typename T, int N, int R, int THREADS = 0>
+template <typename T, int N, int R, int THREADS = 0, bool CPH = false, bool PRE = false>
 constexpr size_t xpass_smem() {
     return ((size_t)xpass_rows<N, R, THREADS>() * 3 * N + tw_off<T>(xpass_rows<N, R, THREADS>() * smem_ld<T>(N))) *
                sizeof(cplx<T>) +
-           FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
+           FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16 +
+           (CPH ? (size_t)xpass_cph_entries<N, PRE>() * sizeof(float2) : 0);
 }
 
 // Column-pass modes: the kinetic factor (FFT, x ph, iFFT), a forward FFT only, the
@@ -290,6 +315,9 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
     V* buf = reinterpret_cast<V*>(smraw);                                   // [2][SB]
     twel<T>* tws = reinterpret_cast<twel<T>*>(buf + 2 * SB);
     uint64_t* bar = reinterpret_cast<uint64_t*>(tws + TWN);
+    // the phase table, copied once per (persistent) block: its global loads sat between
+    // the two transforms of every tile
+    twel<T>* phs = reinterpret_cast<twel<T>*>(bar + 2);
     const int col = threadIdx.x % COLS, t = threadIdx.x / COLS;
     const void* map = &tmap;
 
@@ -338,6 +366,7 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
         if (first + stride < a.n_tiles) issue_load(first + stride, 1);
     }
     copy_table(tws, a.tw, TWN);
+    if constexpr (!FWD_ONLY) copy_table(phs, a.ph, N);
     __syncthreads();
     int it = 0;
     int failed_tile = -1;
@@ -360,7 +389,7 @@ k_colpass_tma(const __grid_constant__ CUtensorMap tmap, const ColTmaArgs<T> a) {
         fft_pencil<N, R, -1, 1, Sync::Block>(v, xb, tws, t);
         if constexpr (!FWD_ONLY) {
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], a.ph[t + m * TP]);
+            for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], phs[t + m * TP]);
             fft_pencil<N, R, +1, 1, Sync::Block>(v, xb, tws, t);
         }
 #pragma unroll
@@ -434,15 +463,17 @@ inline cudaError_t launch_with_smem(K kernel, int grid, int block, size_t smem, 
     return cudaLaunchKernel((const void*)kernel, dim3(grid), dim3(block), args, smem, s);
 }
 
-template <typename T, int N, int THREADS = 0>
+template <typename T, int N, int THREADS = 0, bool CPH = false>
 cudaError_t xpass_n(bool pre, const PassArgs<T>& a, cudaStream_t s) {
     constexpr int R = Tune<T>::kXR;
     constexpr int TP = N / R;
     constexpr int RPC = xpass_rows<N, R, THREADS>();
     const int64_t grid = (a.total_rows + RPC - 1) / RPC;
-    const size_t smem = xpass_smem<T, N, R, THREADS>();
-    if (pre) return launch_with_smem(k_xpass<T, N, R, true, THREADS>, (int)grid, RPC * TP, smem, s, &a);
-    return launch_with_smem(k_xpass<T, N, R, false, THREADS>, (int)grid, RPC * TP, smem, s, &a);
+    if (pre)
+        return launch_with_smem(k_xpass<T, N, R, true, THREADS, CPH>, (int)grid, RPC * TP,
+                                xpass_smem<T, N, R, THREADS, CPH, true>(), s, &a);
+    return launch_with_smem(k_xpass<T, N, R, false, THREADS, CPH>, (int)grid, RPC * TP,
+                            xpass_smem<T, N, R, THREADS, CPH, false>(), s, &a);
 }
 
 // Block sizes the FP32 x pass is built for (the tuner's candidates); 0 = the default.
@@ -468,7 +499,8 @@ template <typename T, int N, int COLS, bool FWD_ONLY, bool ZPASS>
 cudaError_t colpass_tma_n(const CUtensorMap& map, const ColTmaArgs<T>& a, int sms, cudaStream_t s) {
     constexpr int R = Tune<T>::kColR(N);
     constexpr int THREADS = COLS * (N / R);
-    const size_t smem = colpass_tma_smem<T, N, COLS>() + FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16;
+    const size_t smem = colpass_tma_smem<T, N, COLS>() + FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16 +
+                        (FWD_ONLY ? 0 : (size_t)N * sizeof(twel<T>));
     auto kern = k_colpass_tma<T, N, R, COLS, FWD_ONLY, ZPASS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

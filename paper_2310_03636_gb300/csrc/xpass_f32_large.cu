@@ -1,0 +1,32 @@
+// FP32 x pass instantiations for x extents 512, 1024 (split from the other
+// passes so the translation units compile in parallel).
+#include "prop_kernels.cuh"
+
+namespace gpe {
+
+namespace {
+
+// With compact phase tables (a.phc set) the x pass is built for 128 and 256 threads (0: the
+// default size); without them only for the default size.
+template <int NN>
+static cudaError_t xpass_threads(int threads, bool pre, const PassArgs<float>& a, cudaStream_t s) {
+    if (!a.phc) return threads == 0 ? xpass_n<float, NN>(pre, a, s) : cudaErrorInvalidValue;
+    if (threads == 0) threads = xpass_rows<NN, Tune<float>::kXR>() * (NN / Tune<float>::kXR);
+    switch (threads) {
+        case 128: return xpass_n<float, NN, 128, true>(pre, a, s);
+        case 256: return xpass_n<float, NN, 256, true>(pre, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_xpass_f32_large(int n, bool pre, const PassArgs<float>& a, cudaStream_t s, int threads) {
+    switch (n) {
+        case 512: return xpass_threads<512>(threads, pre, a, s);
+        case 1024: return xpass_threads<1024>(threads, pre, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gpe

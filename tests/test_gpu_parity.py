@@ -117,6 +117,29 @@ def test_propagation_fp32_3d_200_steps(B):
     b.close()
 
 
+@pytest.mark.parametrize("shape", [(64, 128), (32 * 4, 512)])
+def test_fp32_kinetic_angles_beyond_half_pi(B, shape):
+    """dt and dx with kinetic phases dt k^2/2 up to 2 rad at the largest k: the tables then
+    carry a sign per entry and the x pass reads them from global memory (no compact
+    table); same parity bar, and the x-pass block size is not selectable there.  Weak
+    couplings and noise keep the nonlinear phases small (with c0 = 1 and 2 particles per
+    site at dx = 1/2 they reach ~1 rad per step and the chaotic growth of rounding errors,
+    the same in FP64, dominates after a few tens of such steps)."""
+    dx, dt, steps, seed = 0.5, 0.1, 40, 12
+    c0, c1 = 0.1, -0.01
+    b = B.GPEBatch(shape, 2, "c64", c0, c1, Q, dt, dx=dx)
+    b.init_noise(seed, MEAN, 0.05)
+    b.step(steps)
+    assert b.sync_status() == B.GPE_OK
+    gpu = b.psi.cpu().numpy().astype(np.complex128)
+    ref = run_oracle(oracle_initial(shape, 2, seed, dx=dx, npm=0.05), dt, steps, 2, c0=c0, c1=c1, dx=dx)
+    assert rel_l2_per_comp(gpu, ref) <= 1e-4
+    with pytest.raises(B.GPEError) as ei:
+        b.set_xpass_threads(128)
+    assert ei.value.status == B.GPE_EUNSUPPORTED
+    b.close()
+
+
 def test_split_calls_and_time_dependent_q(B):
     """q(t) ramp through knots, advanced in uneven chunks: same as the oracle's single run."""
     shape, ntraj, dt, seed = (64, 64), 2, 0.02, 5
