@@ -405,6 +405,41 @@ __device__ __forceinline__ void local_step(V& p1, V& p0, V& pm, const LocalCoef<
     local_step<false, T>(p1, p0, pm, k, SitePot<T>{(T)0, (T)0, (T)0});
 }
 
+// The local step (no potential) over the sites i0, i0 + stride, ... below n of three
+// component arrays (site i of component c at bc[idx(i)]): the FP32 paper scheme two sites
+// at a time in packed instructions, any site left over (and every other case) one at a
+// time.
+template <typename T, typename V, typename IDX>
+__device__ __forceinline__ void local_step_sites(V* b0, V* b1, V* b2, int i0, int n, int stride,
+                                                 const LocalCoef<T>& k, IDX idx) {
+    int i = i0;
+    if constexpr (sizeof(T) == 4) {
+        if (k.kind == 0) {
+#pragma unroll 1
+            for (; i + stride < n; i += 2 * stride) {
+                const int ka = idx(i), kb = idx(i + stride);
+                cpair p1 = pack_pair(b0[ka], b0[kb]), p0 = pack_pair(b1[ka], b1[kb]), pm = pack_pair(b2[ka], b2[kb]);
+                local_step_pair(p1, p0, pm, k);
+                b0[ka] = lane_x(p1);
+                b0[kb] = lane_y(p1);
+                b1[ka] = lane_x(p0);
+                b1[kb] = lane_y(p0);
+                b2[ka] = lane_x(pm);
+                b2[kb] = lane_y(pm);
+            }
+        }
+    }
+#pragma unroll 2
+    for (; i < n; i += stride) {
+        const int kk = idx(i);
+        V p1 = b0[kk], p0 = b1[kk], pm = b2[kk];
+        local_step<T>(p1, p0, pm, k);
+        b0[kk] = p1;
+        b1[kk] = p0;
+        b2[kk] = pm;
+    }
+}
+
 // Potential of site i from a [3][sites] array (comp_stride = sites), or zero.
 template <typename T>
 __device__ __forceinline__ SitePot<T> site_pot(const T* __restrict__ vpot, int64_t comp_stride, int64_t i) {

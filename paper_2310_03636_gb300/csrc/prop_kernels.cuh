@@ -156,33 +156,8 @@ k_xpass(const PassArgs<T> a) {
             kinetic_row<T, N, R, RPC, CPH>(Dr + c * N, Xr, tws, a.ph_pre, t, phc + (N / 2 + 1), a.ph_scale);
     }
     if (lrow < nrows) {
-        if (sizeof(T) == 4 && a.vpot == nullptr && a.coef.kind == 0) {
-            // the FP32 step of the paper's scheme two sites at a time (packed instructions)
-            if constexpr (sizeof(T) == 4) {
-#pragma unroll 1
-                for (int m = 0; m < R; m += 2) {
-                    const int i = t + m * TP, j = i + TP;
-                    cpair p1 = pack_pair(Dr[i], Dr[j]), p0 = pack_pair(Dr[N + i], Dr[N + j]),
-                          pm = pack_pair(Dr[2 * N + i], Dr[2 * N + j]);
-                    local_step_pair(p1, p0, pm, a.coef);
-                    Dr[i] = lane_x(p1);
-                    Dr[j] = lane_y(p1);
-                    Dr[N + i] = lane_x(p0);
-                    Dr[N + j] = lane_y(p0);
-                    Dr[2 * N + i] = lane_x(pm);
-                    Dr[2 * N + j] = lane_y(pm);
-                }
-            }
-        } else if (a.vpot == nullptr) {
-#pragma unroll 2
-            for (int m = 0; m < R; ++m) {
-                const int i = t + m * TP;
-                V p1 = Dr[i], p0 = Dr[N + i], pm = Dr[2 * N + i];
-                local_step<T>(p1, p0, pm, a.coef);
-                Dr[i] = p1;
-                Dr[N + i] = p0;
-                Dr[2 * N + i] = pm;
-            }
+        if (a.vpot == nullptr) {
+            local_step_sites<T>(Dr, Dr + N, Dr + 2 * N, t, N, TP, a.coef, [](int i) { return i; });
         } else {
             const int64_t g = row0 + lrow;
             const int64_t traj = g / a.rows_per_traj;

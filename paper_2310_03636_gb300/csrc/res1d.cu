@@ -99,15 +99,7 @@ k_resident1d(const Res1DArgs<T> a) {
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
         if (a.vpot == nullptr) {
-#pragma unroll 2
-            for (int i = tid; i < N; i += NT) {
-                const int k = spad(i);
-                V p1 = buf[0][k], p0 = buf[1][k], pm = buf[2][k];
-                local_step<T>(p1, p0, pm, coef);
-                buf[0][k] = p1;
-                buf[1][k] = p0;
-                buf[2][k] = pm;
-            }
+            local_step_sites<T>(buf[0], buf[1], buf[2], tid, N, NT, coef, [](int i) { return spad(i); });
         } else {
 #pragma unroll 2
             for (int i = tid; i < N; i += NT) {

@@ -124,15 +124,7 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
         if (a.vpot == nullptr) {
-#pragma unroll 2
-            for (int i = t; i < M; i += TP) {
-                const int k = spad(i);
-                V p1 = buf[k], p0 = buf[LD + k], pm = buf[2 * LD + k];
-                local_step<T>(p1, p0, pm, coef);
-                buf[k] = p1;
-                buf[LD + k] = p0;
-                buf[2 * LD + k] = pm;
-            }
+            local_step_sites<T>(buf, buf + LD, buf + 2 * LD, t, M, TP, coef, [](int i) { return spad(i); });
         } else {
 #pragma unroll 2
             for (int i = t; i < M; i += TP) {
