@@ -110,8 +110,10 @@ gpe_status gpe_step_batch(gpe_batch* batch, int64_t nsteps, void* stream);
 
 /* Accumulates observables of the current fields into acc (caller-owned device FP64):
  * acc += contributions, at offset sample_slot * slot_doubles (see gpe_obs_layout).
- * Within one slot: [4][nbins] spectra sums (quantity order n_1, n_0, n_-1, S_perp),
- * each the sum over trajectories and over the grid modes of a bin of
+ * Within one slot: [4][nbins] spectra sums (quantity order n_1, n_0, n_-1, S_perp) --
+ * a batch of several shapes has one such block per shape group with equal side lengths,
+ * one after the other in group order (gpe_obs_group_layout), a single shape just one --
+ * each the sum over the group's trajectories and over the grid modes of a bin of
  *   n_m(k) = |A_m(k)|^2 - 1/2,  A_m(k) = dx^d / sqrt(L^d) sum_x psi_m(x) e^{-ik.x},
  *   S_perp(k) = |F_perp(k)|^2 / L^d,  F_perp(k) = dx^d sum_x F_perp(x) e^{-ik.x},
  *   F_perp = sqrt(2) (psi_1^* psi_0 + psi_0^* psi_-1)   (Sec. 2.1),
@@ -126,16 +128,23 @@ gpe_status gpe_step_batch(gpe_batch* batch, int64_t nsteps, void* stream);
  * on a batch allocates the handle's spectra workspace (four fields per trajectory, in
  * chunks of at most 1 GiB); make it before capturing a stream.
  * Errors: GPE_EINVAL (NULL acc, sample_slot < 0, unknown flags), GPE_EUNSUPPORTED
- * (spectra requested for a batch with more than one shape or unequal sides; the winding
- * number for a batch with 2D or 3D trajectories).  The winding number alone allocates no workspace. */
+ * (spectra requested for a batch in which no shape group has equal side lengths; the
+ * winding number for a batch with 2D or 3D trajectories).  Groups with unequal sides add
+ * diagnostics but no spectra.  The winding number alone allocates no workspace. */
 gpe_status observables_accumulate(gpe_batch* batch, double* acc, uint32_t flags,
                                   int32_t sample_slot, void* stream);
 
-/* Accumulator geometry: number of radial bins (0 if spectra are unavailable) and the
- * number of doubles per sample slot (4 * nbins + 9 * ntraj). */
+/* Accumulator geometry: number of radial bins of all shape groups together (0 if spectra
+ * are unavailable) and the number of doubles per sample slot (4 * nbins + 9 * ntraj). */
 gpe_status gpe_obs_layout(const gpe_batch* batch, int32_t* nbins, int64_t* slot_doubles);
 
-/* Number of grid modes in each radial bin (host array of nbins int64). */
+/* Spectra block of trajectory traj's shape group: its number of radial bins (0 if the
+ * group has unequal sides) and the offset, in doubles from the start of a slot, of its
+ * [4][nbins] block.  Errors: GPE_EINVAL. */
+gpe_status gpe_obs_group_layout(const gpe_batch* batch, int32_t traj, int32_t* nbins, int64_t* spectra_offset);
+
+/* Number of grid modes in each radial bin (host array of nbins int64; the groups' bins one
+ * after the other, as in the slot). */
 gpe_status gpe_bin_counts(const gpe_batch* batch, int64_t* counts);
 
 /* Offset added to the batch's trajectory indices in the noise counter (default 0), so

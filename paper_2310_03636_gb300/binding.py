@@ -53,6 +53,7 @@ def _load():
         "observables_accumulate": ([vp, vp, u32, i32, vp], ctypes.c_int),
         "gpe_obs_layout": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], ctypes.c_int),
         "gpe_bin_counts": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "gpe_obs_group_layout": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)], ctypes.c_int),
         "gpe_batch_get_step": ([vp], i64),
         "gpe_batch_set_step": ([vp, i64], ctypes.c_int),
         "gpe_sync_status": ([vp, vp], ctypes.c_int),
@@ -312,6 +313,13 @@ class GPEBatch:
 
     def observables(self, acc, flags=GPE_OBS_SPECTRA | GPE_OBS_DIAG, slot=0, stream=None):
         observables_accumulate(self.h, acc, flags, slot, stream)
+
+    def group_layout(self, traj=0):
+        """(nbins, spectra_offset) of trajectory traj's shape group within a slot."""
+        nb = ctypes.c_int32()
+        off = ctypes.c_int64()
+        _check(LIB.gpe_obs_group_layout(self.h, int(traj), ctypes.byref(nb), ctypes.byref(off)))
+        return nb.value, off.value
 
     def bin_counts(self):
         nb, _ = self.layout()

@@ -869,7 +869,7 @@ gpe_status observables_accumulate(gpe_batch* b, double* acc, uint32_t flags, int
     if (slot < 0) return fail(GPE_EINVAL, "sample_slot < 0");
     if (flags & ~(GPE_OBS_SPECTRA | GPE_OBS_DIAG | GPE_OBS_WINDING)) return fail(GPE_EINVAL, "unknown flags 0x%x", flags);
     if ((flags & GPE_OBS_SPECTRA) && b->obs.nbins <= 0)
-        return fail(GPE_EUNSUPPORTED, "spectra need one shape with equal side lengths");
+        return fail(GPE_EUNSUPPORTED, "spectra need a shape group with equal side lengths");
     const double q = q_at_host(b, (double)b->step * b->p.dt);
     ProfScope ps(b, 4, (cudaStream_t)stream, obs_launches(b->obs, b->groups, flags));
     gpe_status s = obs_accumulate(b->obs, b->groups, b->dtype == GPE_C128, b->p.c0, b->p.c1, q, acc, flags, slot,
@@ -883,6 +883,19 @@ gpe_status gpe_obs_layout(const gpe_batch* b, int32_t* nbins, int64_t* slot_doub
     *nbins = b->obs.nbins;
     *slot_doubles = (int64_t)4 * (b->obs.nbins > 0 ? b->obs.nbins : 0) + 9 * (int64_t)b->trajs.size();
     return GPE_OK;
+}
+
+gpe_status gpe_obs_group_layout(const gpe_batch* b, int32_t traj, int32_t* nbins, int64_t* spectra_offset) {
+    if (!b || !nbins || !spectra_offset || traj < 0 || traj >= (int32_t)b->trajs.size())
+        return fail(GPE_EINVAL, "bad batch, trajectory or NULL argument");
+    for (size_t k = 0; k < b->groups.size(); ++k)
+        for (int id : b->groups[k].ids)
+            if (id == traj) {
+                *nbins = k < b->obs.gbins.size() ? b->obs.gbins[k].nbins : 0;
+                *spectra_offset = k < b->obs.gbins.size() ? 4 * b->obs.gbins[k].offset : 0;
+                return GPE_OK;
+            }
+    return fail(GPE_EINVAL, "trajectory %d not found", traj);
 }
 
 gpe_status gpe_bin_counts(const gpe_batch* b, int64_t* counts) {

@@ -22,6 +22,7 @@
 #include <string>
 #include <vector>
 
+#include "adjoint.h"
 #include "fft.cuh"
 #include "obs.h"
 
@@ -277,8 +278,8 @@ k_obs_winding(cplx<T>* const* __restrict__ ptrs, const int32_t* __restrict__ ids
 }
 
 template <typename T>
-gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q, double* acc, uint32_t flags,
-                     int slot, int* d_status, cudaStream_t s) {
+gpe_status run_group(ObsWork& w, const Group& g, const GroupBins& gb, double c0, double c1, double q, double* acc,
+                     uint32_t flags, int slot, int* d_status, cudaStream_t s) {
     using V = cplx<T>;
     const int64_t nb4 = 4 * (int64_t)(w.nbins > 0 ? w.nbins : 0);
     const int64_t slot_doubles = nb4 + 9 * w.ntraj_total;
@@ -315,6 +316,12 @@ gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q,
             e = launch_rowfft<T>(g.n[0], W, (int64_t)nc * 4 * g.n[1] * g.n[2], twx, s);
         }
         if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs x fft", e);
+        if (g.ndim > 1) {
+            // the chunk's 4-field blocks lie back to back at this group's size (as k_obs_prep
+            // wrote them and the x transform read them), not at the largest group's
+            e = launch_fill_ptrs(w.d_Wptrs, W, (int64_t)4 * g.sites * (int64_t)sizeof(V), nc, s);
+            if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs workspace pointers", e);
+        }
         for (int ax = 1; ax < g.ndim; ++ax) {
             PassArgs<T> a{};
             a.ptrs = reinterpret_cast<V* const*>(w.d_Wptrs);
@@ -352,9 +359,10 @@ gpe_status run_group(ObsWork& w, const Group& g, double c0, double c1, double q,
             e = cudaGetLastError();
             if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs diagnostics", e);
         }
-        if (flags & GPE_OBS_SPECTRA) {
-            k_obs_bins<T><<<dim3(w.nbins, 4), kThreads, 0, s>>>(W, g.sites, nc, w.d_off, w.d_modes,
-                                                               vol / (double)g.sites, acc_slot, w.nbins);
+        if ((flags & GPE_OBS_SPECTRA) && gb.nbins > 0) {
+            k_obs_bins<T><<<dim3(gb.nbins, 4), kThreads, 0, s>>>(W, g.sites, nc, gb.d_off, gb.d_modes,
+                                                                vol / (double)g.sites, acc_slot + 4 * gb.offset,
+                                                                gb.nbins);
             e = cudaGetLastError();
             if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "obs bins", e);
         }
@@ -376,30 +384,25 @@ const char* obs_last_error() { return g_obs_err.c_str(); }
 
 int64_t obs_launches(const ObsWork& w, const std::vector<Group>& groups, uint32_t flags) {
     int64_t n = 0;
-    for (const Group& g : groups) {
+    for (size_t k = 0; k < groups.size(); ++k) {
+        const Group& g = groups[k];
         const int64_t chunk = w.ready ? w.chunk : 0;
         int64_t max_traj = 0;
         for (const Group& h : groups) max_traj = std::max<int64_t>(max_traj, h.ntraj);
         const int64_t c = chunk > 0 ? chunk : max_traj;  // before the first call: estimate
         const int64_t nchunks = (g.ntraj + c - 1) / c;
         const bool fields = flags & (GPE_OBS_SPECTRA | GPE_OBS_DIAG);
-        const int64_t per = (fields ? 1 + g.ndim + (g.cluster > 0 ? 1 : 0) : 0) + ((flags & GPE_OBS_DIAG) ? 2 : 0) +
-                            ((flags & GPE_OBS_SPECTRA) ? 1 : 0);
+        const bool spectra = (flags & GPE_OBS_SPECTRA) && k < w.gbins.size() && w.gbins[k].nbins > 0;
+        const int64_t per = (fields ? 1 + g.ndim + (g.cluster > 0 ? 1 : 0) + (g.ndim > 1 ? 1 : 0) : 0) +
+                            ((flags & GPE_OBS_DIAG) ? 2 : 0) + (spectra ? 1 : 0);
         n += nchunks * per + ((flags & GPE_OBS_WINDING) ? 1 : 0);
     }
     return n;
 }
 
-gpe_status obs_init(ObsWork& w, const std::vector<Group>& groups, bool f64, int) {
-    w.f64 = f64;
-    w.ntraj_total = 0;
-    for (const Group& g : groups) w.ntraj_total += g.ntraj;
-    w.nbins = 0;
-    if (groups.size() != 1) return GPE_OK;
-    const Group& g = groups[0];
-    for (int a = 1; a < g.ndim; ++a)
-        if (g.n[a] != g.n[0]) return GPE_OK;
-    const int n = g.n[0];
+// Bin tables of one group with equal side lengths (radial bins b = round(|j|) of the folded
+// mode vector, in the mode order the group's transforms leave), appended to w.counts.
+static gpe_status group_bins(ObsWork& w, const Group& g, GroupBins& gb) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     int lm = 0, lc = 0;   // four-step order of 1D cluster groups (see k_obs_cross)
     if (g.cluster > 0) {
@@ -415,31 +418,56 @@ gpe_status obs_init(ObsWork& w, const std::vector<Group>& groups, bool f64, int)
         bin[i] = (int32_t)b;
         if (b > maxb) maxb = b;
     }
-    (void)n;
-    w.nbins = (int)(maxb + 1);
-    w.counts.assign(w.nbins, 0);
-    for (int64_t i = 0; i < g.sites; ++i) w.counts[bin[i]]++;
-    std::vector<int32_t> off(w.nbins + 1, 0), modes(g.sites);
-    for (int b = 0; b < w.nbins; ++b) off[b + 1] = off[b] + (int32_t)w.counts[b];
+    gb.nbins = (int)(maxb + 1);
+    std::vector<int64_t> counts(gb.nbins, 0);
+    for (int64_t i = 0; i < g.sites; ++i) counts[bin[i]]++;
+    std::vector<int32_t> off(gb.nbins + 1, 0), modes(g.sites);
+    for (int b = 0; b < gb.nbins; ++b) off[b + 1] = off[b] + (int32_t)counts[b];
     std::vector<int32_t> fill(off.begin(), off.end() - 1);
     for (int64_t i = 0; i < g.sites; ++i) modes[fill[bin[i]]++] = (int32_t)i;
-    cudaError_t e = device_malloc((void**)&w.d_off, sizeof(int32_t) * (w.nbins + 1));
-    if (e == cudaSuccess) e = device_malloc((void**)&w.d_modes, sizeof(int32_t) * g.sites);
+    cudaError_t e = device_malloc((void**)&gb.d_off, sizeof(int32_t) * (gb.nbins + 1));
+    if (e == cudaSuccess) e = device_malloc((void**)&gb.d_modes, sizeof(int32_t) * g.sites);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(w.d_off);
-        w.d_off = nullptr;
+        cudaFree(gb.d_off);
+        gb.d_off = nullptr;
         return obs_fail(GPE_ENOMEM, "bin tables", e);
     }
-    e = cudaMemcpy(w.d_off, off.data(), sizeof(int32_t) * (w.nbins + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(w.d_modes, modes.data(), sizeof(int32_t) * g.sites, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(gb.d_off, off.data(), sizeof(int32_t) * (gb.nbins + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(gb.d_modes, modes.data(), sizeof(int32_t) * g.sites, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return obs_fail(GPE_ECUDA, "copy bin tables", e);
+    w.counts.insert(w.counts.end(), counts.begin(), counts.end());
+    return GPE_OK;
+}
+
+// Bins for every shape group whose side lengths are equal; each group's spectra get a
+// block of their own in the accumulator slot, in group order.
+gpe_status obs_init(ObsWork& w, const std::vector<Group>& groups, bool f64, int) {
+    w.f64 = f64;
+    w.ntraj_total = 0;
+    for (const Group& g : groups) w.ntraj_total += g.ntraj;
+    w.nbins = 0;
+    w.counts.clear();
+    w.gbins.assign(groups.size(), GroupBins());
+    for (size_t k = 0; k < groups.size(); ++k) {
+        const Group& g = groups[k];
+        bool equal = true;
+        for (int a = 1; a < g.ndim; ++a) equal = equal && g.n[a] == g.n[0];
+        if (!equal) continue;
+        GroupBins& gb = w.gbins[k];
+        gb.offset = w.nbins;
+        const gpe_status s = group_bins(w, g, gb);
+        if (s != GPE_OK) return s;
+        w.nbins += gb.nbins;
+    }
     return GPE_OK;
 }
 
 void obs_free(ObsWork& w) {
-    cudaFree(w.d_off);
-    cudaFree(w.d_modes);
+    for (GroupBins& gb : w.gbins) {
+        cudaFree(gb.d_off);
+        cudaFree(gb.d_modes);
+    }
     cudaFree(w.d_W);
     cudaFree(w.d_Wptrs);
     cudaFree(w.d_part);
@@ -502,9 +530,11 @@ gpe_status obs_accumulate(ObsWork& w, const std::vector<Group>& groups, bool f64
         if (st != GPE_OK) return st;
     }
     gpe_status st = GPE_OK;
-    for (const Group& g : groups) {
-        st = f64 ? run_group<double>(w, g, c0, c1, q, acc, flags, slot, d_status, s)
-                 : run_group<float>(w, g, c0, c1, q, acc, flags, slot, d_status, s);
+    for (size_t k = 0; k < groups.size(); ++k) {
+        const Group& g = groups[k];
+        const GroupBins& gb = w.gbins[k];
+        st = f64 ? run_group<double>(w, g, gb, c0, c1, q, acc, flags, slot, d_status, s)
+                 : run_group<float>(w, g, gb, c0, c1, q, acc, flags, slot, d_status, s);
         if (st != GPE_OK) return st;
     }
     return GPE_OK;

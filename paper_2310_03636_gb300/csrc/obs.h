@@ -10,11 +10,19 @@
 
 namespace gpe {
 
-struct ObsWork {
-    int nbins = 0;                   // radial bins (0: spectra unavailable for this batch)
-    std::vector<int64_t> counts;     // modes per bin
+// Radial bins of one shape group: its spectra sit in each accumulator slot at
+// 4 * offset doubles, laid out [field][bin] over its nbins bins.
+struct GroupBins {
+    int nbins = 0;                   // 0: no spectra for the group (unequal side lengths)
+    int64_t offset = 0;              // bins of the groups before it
     int32_t* d_off = nullptr;        // CSR offsets over bins (nbins + 1)
     int32_t* d_modes = nullptr;      // mode indices sorted by bin, then by index
+};
+
+struct ObsWork {
+    int nbins = 0;                   // radial bins of all groups (0: spectra unavailable for this batch)
+    std::vector<int64_t> counts;     // modes per bin, the groups' bins one after the other
+    std::vector<GroupBins> gbins;    // per shape group
     void* d_W = nullptr;             // workspace: chunk x 4 fields x sites complex
     void** d_Wptrs = nullptr;        // per chunk slot: its 4-field block
     double* d_part = nullptr;        // chunk x nblk x 7 real-space partial sums

@@ -185,9 +185,10 @@ def test_smooth_field_dx_and_couplings(B):
 
 
 def test_ragged_batch(B):
-    """Trajectories of different shapes in one batch, each matches the oracle."""
-    import ctypes
-    shapes = [(256,), (64, 64), (128,), (64, 64)]
+    """Trajectories of different shapes in one batch, each matches the oracle; spectra per
+    shape group (one block per group in the slot) and per-trajectory diagnostics match the
+    oracle's, a group with unequal sides adds diagnostics but no spectra."""
+    shapes = [(256,), (64, 64), (128,), (64, 64), (64, 128), (8192,)]
     b = B.GPEBatch(list(shapes), dtype="c128", dt=0.02)
     b.init_noise(31, MEAN, 0.5)
     b.step(40)
@@ -195,17 +196,41 @@ def test_ragged_batch(B):
         ref = run_oracle(oracle_initial(s, 1, 31, ids=[i]), 0.02, 40, len(s))
         assert rel_l2_per_comp(b.psi[i].cpu().numpy()[None], ref) <= 1e-11
     nb, sd = b.layout()
-    assert nb == 0 and sd == 9 * 4
+    nt = len(shapes)
+    assert sd == 4 * nb + 9 * nt
+    # bins: 1D 256 -> 129, 2D 64^2 -> 46, 1D 128 -> 65, 64 x 128 none, 1D 8192 -> 4097
+    assert nb == 129 + 46 + 65 + 4097
     acc = torch.zeros(sd, dtype=torch.float64, device="cuda")
-    with pytest.raises(B.GPEError) as ei:
-        b.observables(acc, B.GPE_OBS_SPECTRA, 0)
-    assert ei.value.status == B.GPE_EUNSUPPORTED
-    b.observables(acc, B.GPE_OBS_DIAG, 0)
-    diag = acc.cpu().numpy()[:32].reshape(4, 8)
+    b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 0)
+    assert b.sync_status() == B.GPE_OK
+    a = acc.cpu().numpy()
+    counts = b.bin_counts()
+    groups = {}
+    for i, s in enumerate(shapes):
+        groups.setdefault(s, []).append(i)
+    for s, ids in groups.items():
+        gnb, off = b.group_layout(ids[0])
+        if len(set(s)) > 1:
+            assert gnb == 0
+            continue
+        psi = np.stack([b.psi[i].cpu().numpy() for i in ids])
+        rs, _, rc = oracle_observables(psi, 1.0, len(s))
+        assert gnb == rs.shape[1]
+        got = a[off:off + 4 * gnb].reshape(4, gnb)
+        np.testing.assert_array_equal(counts[off // 4:off // 4 + gnb], rc)
+        assert np.abs(got - rs).max() <= 1e-10 * np.abs(rs).max(), s
+    diag = a[4 * nb:4 * nb + 8 * nt].reshape(nt, 8)
     for i, s in enumerate(shapes):
         p = torch.as_tensor(b.psi[i].cpu().numpy())
         ref = O.diagnostics(p, 1.0, C0, C1, Q, len(s)).numpy()
         np.testing.assert_allclose(diag[i], ref, rtol=1e-10, atol=1e-9)
+    b.close()
+    # no group with equal sides: spectra refused
+    b = B.GPEBatch([(64, 128), (128, 64)], dtype="c128", dt=0.02)
+    acc = b.new_accumulator(1)
+    with pytest.raises(B.GPEError) as ei:
+        b.observables(acc, B.GPE_OBS_SPECTRA, 0)
+    assert ei.value.status == B.GPE_EUNSUPPORTED
     b.close()
 
 
