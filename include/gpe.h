@@ -244,6 +244,20 @@ gpe_status gpe_batch_get_xpass_threads(const gpe_batch* batch, int32_t traj, int
 int64_t gpe_batch_get_step(const gpe_batch* batch);
 gpe_status gpe_batch_set_step(gpe_batch* batch, int64_t step);
 
+/* Checkpoint and resume (the paper has no counterpart; long runs and preemptible jobs need
+ * it).  save: synchronises ``stream`` and writes to ``path`` (host file) the batch's step
+ * counter (which also fixes the position in a q(t) schedule), trajectory base, dtype,
+ * integrator, couplings, q knots, every trajectory's shape and spacing, and the fields of
+ * every trajectory, with a hash of the whole.  load: reads such a file into a batch of the
+ * same configuration -- the fields are copied into the batch's (caller-owned) field
+ * buffers and the step counter and trajectory base are restored; the noise is drawn only
+ * by tw_init_noise, so there is no generator state.  FP64 accumulators are the caller's
+ * and are not included.  Errors: GPE_EINVAL (NULL arguments, unreadable or unwritable
+ * file, not a checkpoint, hash mismatch, another configuration or size), GPE_ENOMEM
+ * (host buffer), GPE_ECUDA. */
+gpe_status gpe_batch_save(const gpe_batch* batch, const char* path, void* stream);
+gpe_status gpe_batch_load(gpe_batch* batch, const char* path, void* stream);
+
 /* Reverse-mode step (vector-Jacobian product of one Strang step, Sec. 2.2 scheme; the
  * paper itself has no adjoint).  With psi_step_in = psi_n, the fields at the start of
  * step n = step_index (contiguous [ntraj][3][sites] complex, caller-owned device memory,

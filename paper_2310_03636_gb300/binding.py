@@ -56,6 +56,8 @@ def _load():
         "gpe_obs_group_layout": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)], ctypes.c_int),
         "gpe_batch_get_step": ([vp], i64),
         "gpe_batch_set_step": ([vp, i64], ctypes.c_int),
+        "gpe_batch_save": ([vp, ctypes.c_char_p, vp], ctypes.c_int),
+        "gpe_batch_load": ([vp, ctypes.c_char_p, vp], ctypes.c_int),
         "gpe_sync_status": ([vp, vp], ctypes.c_int),
         "gpe_profile_enable": ([vp, i32], ctypes.c_int),
         "gpe_profile_read": ([vp, pd, ctypes.POINTER(i64)], ctypes.c_int),
@@ -334,6 +336,14 @@ class GPEBatch:
 
     def set_step(self, step):
         _check(LIB.gpe_batch_set_step(self.h, int(step)))
+
+    def save(self, path, stream=None):
+        """Write a checkpoint (fields, step, configuration) to the host file ``path``."""
+        _check(LIB.gpe_batch_save(self.h, os.fsencode(str(path)), _stream(stream)))
+
+    def load(self, path, stream=None):
+        """Restore fields and step from a checkpoint of a batch of this configuration."""
+        _check(LIB.gpe_batch_load(self.h, os.fsencode(str(path)), _stream(stream)))
 
     def set_traj_base(self, base):
         _check(LIB.gpe_batch_set_traj_base(self.h, int(base)))

@@ -1261,6 +1261,145 @@ gpe_status gpe_batch_set_graph(gpe_batch* b, int32_t enable) {
     return GPE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Checkpoint file: "GPECKPT1", version, the batch's configuration (dtype, integrator,
+// step, trajectory base, couplings, q knots, every trajectory's shape and spacing), the
+// fields of every trajectory, and an FNV-1a hash of all preceding bytes.
+constexpr char kCkptMagic[8] = {'G', 'P', 'E', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct Writer {
+    std::vector<unsigned char> buf;
+    template <typename X> void put(const X& x) {
+        const unsigned char* p = reinterpret_cast<const unsigned char*>(&x);
+        buf.insert(buf.end(), p, p + sizeof(X));
+    }
+};
+
+struct Reader {
+    const std::vector<unsigned char>& buf;
+    size_t pos = 0;
+    template <typename X> bool get(X& x) {
+        if (pos + sizeof(X) > buf.size()) return false;
+        std::memcpy(&x, buf.data() + pos, sizeof(X));
+        pos += sizeof(X);
+        return true;
+    }
+};
+
+size_t field_bytes(const gpe_batch* b, const gpe_traj& t) {
+    return (size_t)3 * t.n[0] * t.n[1] * t.n[2] * (b->dtype == GPE_C64 ? 8 : 16);
+}
+
+void put_config(Writer& w, const gpe_batch* b) {
+    w.put((int32_t)b->dtype);
+    w.put((int32_t)b->trajs.size());
+    w.put((int32_t)b->integrator);
+    w.put(b->p.c0);
+    w.put(b->p.c1);
+    w.put(b->p.q);
+    w.put(b->p.dt);
+    w.put(b->p.t_end);
+    w.put((int32_t)b->knots.size());
+    for (double k : b->knots) w.put(k);
+    for (const gpe_traj& t : b->trajs) {
+        w.put(t.ndim);
+        for (int a = 0; a < 3; ++a) w.put(t.n[a]);
+        w.put(t.dx);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+gpe_status gpe_batch_save(const gpe_batch* b, const char* path, void* stream) {
+    g_err.clear();
+    if (!b || !path) return fail(GPE_EINVAL, "batch or path is NULL");
+    GPE_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    Writer w;
+    for (char c : kCkptMagic) w.put(c);
+    w.put(kCkptVersion);
+    w.put(b->step);
+    w.put(b->traj_base);
+    put_config(w, b);
+    for (const gpe_traj& t : b->trajs) {
+        const size_t nb = field_bytes(b, t);
+        const size_t at = w.buf.size();
+        try {
+            w.buf.resize(at + nb);
+        } catch (const std::bad_alloc&) {
+            return fail(GPE_ENOMEM, "host buffer of %zu bytes", at + nb);
+        }
+        GPE_CK(cudaMemcpy(w.buf.data() + at, t.psi, nb, cudaMemcpyDeviceToHost));
+    }
+    w.put(fnv1a(w.buf.data(), w.buf.size()));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(GPE_EINVAL, "cannot open %s for writing", path);
+    const size_t wrote = std::fwrite(w.buf.data(), 1, w.buf.size(), f);
+    const int closed = std::fclose(f);
+    if (wrote != w.buf.size() || closed != 0) return fail(GPE_EINVAL, "short write to %s", path);
+    return GPE_OK;
+}
+
+gpe_status gpe_batch_load(gpe_batch* b, const char* path, void* stream) {
+    g_err.clear();
+    if (!b || !path) return fail(GPE_EINVAL, "batch or path is NULL");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(GPE_EINVAL, "cannot open %s", path);
+    std::vector<unsigned char> buf;
+    {
+        unsigned char chunk[1 << 16];
+        size_t n;
+        while ((n = std::fread(chunk, 1, sizeof(chunk), f)) > 0) buf.insert(buf.end(), chunk, chunk + n);
+        std::fclose(f);
+    }
+    if (buf.size() < sizeof(kCkptMagic) + sizeof(uint64_t) ||
+        std::memcmp(buf.data(), kCkptMagic, sizeof(kCkptMagic)) != 0)
+        return fail(GPE_EINVAL, "%s is not a checkpoint of this library", path);
+    uint64_t h = 0;
+    std::memcpy(&h, buf.data() + buf.size() - sizeof(uint64_t), sizeof(uint64_t));
+    if (fnv1a(buf.data(), buf.size() - sizeof(uint64_t)) != h) return fail(GPE_EINVAL, "%s is corrupt (hash)", path);
+    Reader r{buf};
+    r.pos = sizeof(kCkptMagic);
+    uint32_t version = 0;
+    int64_t step = 0, base = 0;
+    if (!r.get(version) || version != kCkptVersion) return fail(GPE_EINVAL, "checkpoint version %u", version);
+    if (!r.get(step) || !r.get(base)) return fail(GPE_EINVAL, "truncated checkpoint");
+    // the configuration must be the batch's own, byte for byte
+    Writer mine;
+    put_config(mine, b);
+    if (r.pos + mine.buf.size() > buf.size() ||
+        std::memcmp(buf.data() + r.pos, mine.buf.data(), mine.buf.size()) != 0)
+        return fail(GPE_EINVAL, "checkpoint of another batch configuration (dtype, integrator, couplings, q knots, "
+                                "shapes or spacing differ)");
+    r.pos += mine.buf.size();
+    size_t need = 0;
+    for (const gpe_traj& t : b->trajs) need += field_bytes(b, t);
+    if (r.pos + need + sizeof(uint64_t) != buf.size()) return fail(GPE_EINVAL, "checkpoint size does not match the batch");
+    GPE_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    for (const gpe_traj& t : b->trajs) {
+        const size_t nb = field_bytes(b, t);
+        GPE_CK(cudaMemcpy(t.psi, buf.data() + r.pos, nb, cudaMemcpyHostToDevice));
+        r.pos += nb;
+    }
+    b->step = step;
+    b->traj_base = base;
+    return GPE_OK;
+}
+
 gpe_status gpe_sync_status(gpe_batch* b, void* stream) {
     g_err.clear();
     if (!b) return fail(GPE_EINVAL, "batch is NULL");
