@@ -214,12 +214,24 @@ __device__ __forceinline__ void stockham_stage(V (&v)[NC][R], V* const (&buf)[NC
                 TW f;
                 if constexpr (SPLIT > 0 && OFF >= SPLIT) f = tws_hi[OFF + (r - 1) * NS + k];
                 else f = tws[OFF + (r - 1) * NS + k];
-                // if every twiddle angle 2 pi r k / (NS RS) of this r is within pi/2, the
-                // table's sign is +1 and the scale is skipped (r is a constant once unrolled)
-                const bool sig = 4 * r * (NS - 1) > NS * RS;
+                if constexpr (sizeof(TW) == 8) {
+                    // FP32 table of (p, u) pairs only: the sign of the reduced rotation is -1
+                    // exactly for angles 2 pi r k / (NS RS) in (pi/2, 3 pi/2)
+                    const int x4 = 4 * r * k;
+                    const bool neg = x4 > NS * RS && x4 < 3 * NS * RS;
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    w[c][r] = sig ? twmul<DIR, true>(w[c][r], f) : twmul<DIR, false>(w[c][r], f);
+                    for (int c = 0; c < NC; ++c) {
+                        const float2 q = lift_rot(w[c][r], DIR < 0 ? f.x : -f.x, DIR < 0 ? f.y : -f.y);
+                        w[c][r] = neg ? make_float2(-q.x, -q.y) : q;
+                    }
+                } else {
+                    // if every twiddle angle 2 pi r k / (NS RS) of this r is within pi/2, the
+                    // table's sign is +1 and the scale is skipped (r is a constant once unrolled)
+                    const bool sig = 4 * r * (NS - 1) > NS * RS;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c)
+                        w[c][r] = sig ? twmul<DIR, true>(w[c][r], f) : twmul<DIR, false>(w[c][r], f);
+                }
             }
         }
 #pragma unroll

@@ -298,6 +298,35 @@ std::vector<float2> compact_phases(const std::vector<float4>& t) {
 }
 std::vector<float2> compact_phases(const std::vector<double2>&) { return {}; }
 
+// FP32 stage twiddles of FftPlan<n, R> as (p, u) pairs, for kernels that take the sign of
+// each rotation from its index (entry r, k of a stage with sub-length ns and radix rs is
+// negative exactly when ns rs < 4 r k < 3 ns rs).  The rule is checked against every
+// entry's stored sign; empty if any differs (the kernels then keep the full table).
+std::vector<float2> pair_twiddles(const std::vector<float4>& t, int n, int R) {
+    int logn = 0, logr = 0;
+    while ((1 << logn) < n) ++logn;
+    while ((1 << logr) < R) ++logr;
+    const int nfull = logn / logr, last = 1 << (logn - nfull * logr), stages = nfull + (last > 1 ? 1 : 0);
+    std::vector<float2> out;
+    int ns = 1;
+    size_t i = 0;
+    for (int st = 0; st < stages; ++st) {
+        const int rs = (st < nfull) ? R : last;
+        if (ns > 1)
+            for (int r = 1; r < rs; ++r)
+                for (int k = 0; k < ns; ++k, ++i) {
+                    const int64_t x4 = 4ll * r * k;
+                    const bool neg = x4 > (int64_t)ns * rs && x4 < 3ll * ns * rs;
+                    if (i >= t.size() || (t[i].z < 0.0f) != neg || std::fabs(t[i].z) != 1.0f) return {};
+                    out.push_back(make_float2(t[i].x, t[i].y));
+                }
+        ns *= rs;
+    }
+    if (out.empty()) out.push_back(make_float2(0.0f, 0.0f));
+    return out.size() == t.size() ? out : std::vector<float2>{};
+}
+std::vector<float2> pair_twiddles(const std::vector<double2>&, int, int) { return {}; }
+
 template <typename T>
 gpe_status build_group_tables(gpe_batch* b, Group& g) {
     for (int a = 0; a < g.ndim; ++a) {
@@ -311,12 +340,15 @@ gpe_status build_group_tables(gpe_batch* b, Group& g) {
         GPE_CK(cudaMemcpy(g.ph_half[a], ph.data(), bytes, cudaMemcpyHostToDevice));
         if (a == 0 && g.ndim >= 2) {
             const std::vector<float2> cf = compact_phases(pf), ch = compact_phases(ph);
-            if (!cf.empty() && !ch.empty()) {
-                const size_t cb = sizeof(float2) * cf.size();
+            const std::vector<float2> t2 = pair_twiddles(stage_twiddles_host<T>(g.n[0], 8), g.n[0], 8);
+            if (!cf.empty() && !ch.empty() && !t2.empty()) {
+                const size_t cb = sizeof(float2) * cf.size(), tb = sizeof(float2) * t2.size();
                 if ((s = dev_alloc(b, &g.phc_full, cb)) != GPE_OK) return s;
                 if ((s = dev_alloc(b, &g.phc_half, cb)) != GPE_OK) return s;
+                if ((s = dev_alloc(b, &g.tw2x, tb)) != GPE_OK) return s;
                 GPE_CK(cudaMemcpy(g.phc_full, cf.data(), cb, cudaMemcpyHostToDevice));
                 GPE_CK(cudaMemcpy(g.phc_half, ch.data(), cb, cudaMemcpyHostToDevice));
+                GPE_CK(cudaMemcpy(g.tw2x, t2.data(), tb, cudaMemcpyHostToDevice));
             }
         }
         for (int ri = 0; ri < 3; ++ri) {
@@ -438,6 +470,7 @@ cudaError_t x_pass(gpe_batch* b, const Group& g, bool pre, bool half_post, doubl
         a.phc = reinterpret_cast<const float2*>(half_post ? g.phc_half : g.phc_full);
         a.phc_pre = reinterpret_cast<const float2*>(g.phc_half);
         a.ph_scale = 1.0f / (float)g.n[0];
+        a.tw2 = reinterpret_cast<const float2*>(g.tw2x);
     }
     a.rows_per_traj = (int64_t)g.n[1] * g.n[2];
     a.total_rows = a.rows_per_traj * g.ntraj;
@@ -525,6 +558,7 @@ int tune_xpass_threads(gpe_batch* b, const Group& g, void* scratch, int nt, cuda
             a.phc = reinterpret_cast<const float2*>(g.phc_full);
             a.phc_pre = reinterpret_cast<const float2*>(g.phc_half);
             a.ph_scale = 1.0f / (float)g.n[0];
+            a.tw2 = reinterpret_cast<const float2*>(g.tw2x);
         }
         a.rows_per_traj = (int64_t)g.n[1] * g.n[2];
         a.total_rows = a.rows_per_traj * nt;

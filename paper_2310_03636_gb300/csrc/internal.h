@@ -40,6 +40,8 @@ struct PassArgs {
     const float2* phc;        // for ph
     const float2* phc_pre;    // for ph_pre
     float ph_scale;           // 1/N
+    const float2* tw2;        // with phc: the x axis stage twiddles (8 points per thread) as
+                              // (p, u) pairs, the sign taken from the index
     int* status;              // device status word (bounded waits that expire)
     uint32_t wait_first;      // row pass: 0 = default limit of the first copy wait, else 1 + its poll limit
 };
@@ -87,7 +89,8 @@ struct Group {
     void* ph_full[3] = {};         // per axis: exp(-i dt k^2/2)/n
     void* ph_half[3] = {};         // per axis: exp(-i dt k^2/4)/n
     void* phc_full = nullptr;      // FP32 x axis: compact (p, u) tables for modes 0..n/2, when
-    void* phc_half = nullptr;      //   every angle is within +-pi/2 (else null)
+    void* phc_half = nullptr;      //   every angle is within +-pi/2 (else null), and the stage
+    void* tw2x = nullptr;          //   twiddles for 8 points per thread as (p, u) pairs
     bool contiguous = false;       // fields back to back from hptrs[0]: tensor-map passes usable
     int cluster = 0;               // 1D on a thread-block cluster: blocks per trajectory (0: off)
     void* tw_local[3] = {};        // cluster 1D: stage twiddles of the per-block length M

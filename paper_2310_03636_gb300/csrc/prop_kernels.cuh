@@ -4,6 +4,7 @@
 #pragma once
 
 #include "fft.cuh"
+#include <type_traits>
 #include <cuda.h>
 
 #include "async_copy.cuh"
@@ -71,8 +72,8 @@ __host__ __device__ constexpr uint32_t first_wait_limit(uint32_t wait_first) {
 // With CPH (FP32) the phases come from a compact table in shared memory: (p, u) of the
 // three-shear rotation for modes 0..N/2 (mode k and N - k share an entry) and the common
 // factor scale = 1/N, the same numbers phmul takes from the full table, so the same bits.
-template <typename T, int N, int R, int RPC = 1, bool CPH = false>
-__device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const twel<T>* tws,
+template <typename T, int N, int R, int RPC = 1, bool CPH = false, typename TW = twel<T>>
+__device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const TW* tws,
                                             const twel<T>* __restrict__ ph, int t, const float2* phc = nullptr,
                                             float scale = 0.0f) {
     using V = cplx<T>;
@@ -116,10 +117,12 @@ k_xpass(const PassArgs<T> a) {
     constexpr int LD = smem_ld<T>(N);
     constexpr int TWN = FftPlan<N, R>::tw_size();
     extern __shared__ __align__(128) unsigned char smraw[];
+    // CPH (FP32): the stage twiddles as (p, u) pairs, the sign taken from the index
+    using TWT = typename std::conditional<CPH, float2, twel<T>>::type;
     V* D = reinterpret_cast<V*>(smraw);                          // [RPC][3][N]
     V* X = D + RPC * 3 * N;                                      // [RPC][LD] exchange
-    twel<T>* tws = reinterpret_cast<twel<T>*>(X + tw_off<T>(RPC * LD));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tws + TWN);
+    TWT* tws = reinterpret_cast<TWT*>(X + tw_off<T>(RPC * LD));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tws + ((TWN + 1) & ~1));
     float2* phc = reinterpret_cast<float2*>(bar + 2);   // CPH: [ph][ph_pre] compact tables
     const int lrow = threadIdx.x / TP, t = threadIdx.x % TP;
     const int64_t row0 = (int64_t)blockIdx.x * RPC;
@@ -137,7 +140,8 @@ k_xpass(const PassArgs<T> a) {
                 bulk_g2s(D + (r * 3 + c) * N, src + c * a.comp_stride, N * sizeof(V), bar);
         }
     }
-    copy_table(tws, a.tw[tw_slot<R>()], TWN);
+    if constexpr (CPH) copy_table(tws, a.tw2, TWN);
+    else copy_table(tws, a.tw[tw_slot<R>()], TWN);
     if constexpr (CPH) {
         copy_table(phc, a.phc, N / 2 + 1);
         if constexpr (PRE) copy_table(phc + (N / 2 + 1), a.phc_pre, N / 2 + 1);
@@ -153,7 +157,7 @@ k_xpass(const PassArgs<T> a) {
     if constexpr (PRE) {
 #pragma unroll 1
         for (int c = 0; c < 3; ++c)
-            kinetic_row<T, N, R, RPC, CPH>(Dr + c * N, Xr, tws, a.ph_pre, t, phc + (N / 2 + 1), a.ph_scale);
+            kinetic_row<T, N, R, RPC, CPH, TWT>(Dr + c * N, Xr, tws, a.ph_pre, t, phc + (N / 2 + 1), a.ph_scale);
     }
     if (lrow < nrows) {
         if (a.vpot == nullptr) {
@@ -174,7 +178,7 @@ k_xpass(const PassArgs<T> a) {
         }
     }
 #pragma unroll 1
-    for (int c = 0; c < 3; ++c) kinetic_row<T, N, R, RPC, CPH>(Dr + c * N, Xr, tws, a.ph, t, phc, a.ph_scale);
+    for (int c = 0; c < 3; ++c) kinetic_row<T, N, R, RPC, CPH, TWT>(Dr + c * N, Xr, tws, a.ph, t, phc, a.ph_scale);
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -194,7 +198,7 @@ template <typename T, int N, int R, int THREADS = 0, bool CPH = false, bool PRE 
 constexpr size_t xpass_smem() {
     return ((size_t)xpass_rows<N, R, THREADS>() * 3 * N + tw_off<T>(xpass_rows<N, R, THREADS>() * smem_ld<T>(N))) *
                sizeof(cplx<T>) +
-           FftPlan<N, R>::tw_size() * sizeof(twel<T>) + 16 +
+           (size_t)((FftPlan<N, R>::tw_size() + 1) & ~1) * (CPH ? sizeof(float2) : sizeof(twel<T>)) + 16 +
            (CPH ? (size_t)xpass_cph_entries<N, PRE>() * sizeof(float2) : 0);
 }
 

@@ -10,7 +10,7 @@ namespace {
 // default size); without them only for the default size.
 template <int NN>
 static cudaError_t xpass_threads(int threads, bool pre, const PassArgs<float>& a, cudaStream_t s) {
-    if (!a.phc) return threads == 0 ? xpass_n<float, NN>(pre, a, s) : cudaErrorInvalidValue;
+    if (!a.phc || !a.tw2) return threads == 0 ? xpass_n<float, NN>(pre, a, s) : cudaErrorInvalidValue;
     if (threads == 0) threads = xpass_rows<NN, Tune<float>::kXR>() * (NN / Tune<float>::kXR);
     switch (threads) {
         case 128: return xpass_n<float, NN, 128, true>(pre, a, s);
