@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the ragged-batch measurement the default run adds under 'secondary'")
     p.add_argument("--workload", choices=["2d", "1d", "3d", "ragged", "adjoint", "paper1d", "paper1d_f64"], default="2d",
                    help="2d: the benchmark workload (default); others print a line for that configuration")
     p.add_argument("--no-autotune", action="store_true",
@@ -446,6 +448,11 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample()
 
+    # the ragged mix, measured after every leg of the headline number (one GPU only)
+    secondary = None
+    if rank == 0 and ws == 1 and not args.no_secondary:
+        secondary = {"ragged": ragged_line(B, steps=3, warmup=2)}
+
     if rank == 0:
         out = {"metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -453,7 +460,7 @@ def run_ours(args):
                "data": "synthetic",
                "config": dict(workload_config(ws), column_tiles={"y": tiles[0], "autotuned": tiles[2]}),
                "per_step": per_step, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-               "gpu_launches": launches, "fp64_plain": fp64, "status": status}
+               "gpu_launches": launches, "fp64_plain": fp64, "status": status, "secondary": secondary}
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -547,6 +554,34 @@ def run_other(args):
            "gpu_launches": B.gpe_launch_count() - l0, "status": b.sync_status(), **extra}
     print(json.dumps(out), flush=True)
     b.close()
+
+
+def ragged_line(B, steps, warmup):
+    """The ragged mix (200 1D trajectories of 1024-16384 points and 32 2D ones of
+    128^2-1024^2, FP32, graph replay), site-updates/s over 250-step intervals, and its
+    perfect-packing bound."""
+    stream = torch.cuda.current_stream()
+    shapes = W.ragged_sizes()
+    b = B.GPEBatch(list(shapes), dtype="c64", c0=1.0, c1=-0.1, q=0.09, dt=0.02)
+    b.set_graph(True)
+    per = 250
+    su = sum(int(np.prod(sh)) for sh in shapes) * 3 * per
+    b.init_noise(W.SEED_BASE, (0.0, 0.0, 1.0, 0.0, 0.0, 0.0), 0.5)
+    for _ in range(warmup):
+        b.step(per)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        b.step(per)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = b.sync_status()
+    b.close()
+    return {"workload": "ragged_200x1d_1k-16k_32x2d_128-1024_c64", "value": su / (ms * 1e-3),
+            "unit": "site-updates/s", "ms_per_step": ms, "steps_per_bench_step": per, "trajectories": len(shapes),
+            "status": st, "scheduling": ragged_scheduling_bound(B, shapes, per, ms)}
 
 
 def fill_count(shape):
