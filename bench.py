@@ -593,11 +593,12 @@ def fill_count(shape):
 
 
 def ragged_scheduling_bound(B, shapes, per, measured_ms):
-    """How far the concurrent per-shape streams are from perfect packing.  Each shape of the
-    mix runs alone with enough trajectories to fill the GPU; its rate there (site-updates/s)
-    is the best any schedule of the mix can give its work, so the sum over shapes of
-    work / full-GPU rate bounds from below the time of one step interval -- for the concurrent
-    streams used here or for a single persistent kernel walking all shapes' work."""
+    """The mix against its shapes run one after another, each filling the GPU.  Each shape
+    runs alone with enough trajectories to fill the GPU; the sum over shapes of the mix's
+    work / that full-GPU rate is the time of a step interval scheduled shape by shape at each
+    shape's best uniform rate -- what a single persistent kernel walking the shapes' work in
+    turn would approach.  The concurrent streams can beat it (efficiency above 1) where
+    shapes bound by different units (on-chip 1D kernels, 2D passes) overlap."""
     from collections import Counter
     per_shape = []
     ideal_s = 0.0
@@ -624,7 +625,8 @@ def ragged_scheduling_bound(B, shapes, per, measured_ms):
                           "ideal_ms": work / rate * 1e3})
     return {"measured_ms_per_step": measured_ms, "ideal_ms_per_step": ideal_s * 1e3,
             "packing_efficiency": ideal_s * 1e3 / measured_ms, "per_shape": per_shape,
-            "note": "ideal = sum over shapes of (the mix's work of that shape / its full-GPU rate)"}
+            "note": "ideal = sum over shapes of (the mix's work of that shape / its full-GPU rate), "
+                    "i.e. the shapes run one after another each filling the GPU"}
 
 
 def run_adjoint(args):
