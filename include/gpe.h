@@ -189,6 +189,20 @@ gpe_status gpe_batch_set_integrator(gpe_batch* batch, int32_t kind);
  * profiling is enabled. */
 gpe_status gpe_batch_set_graph(gpe_batch* batch, int32_t enable);
 
+/* Trajectory lanes (scheduling only; the paper runs many independent trajectories per
+ * GPU, Sec. 2.2, and prescribes no order).  gpe_step_batch splits the trajectories of
+ * each 2D/3D shape group into ``lanes`` consecutive ranges of nearly equal size and
+ * advances each range on its own internal stream (forked from and joined back into the
+ * caller's stream; captured together in graph mode), so that one range's kernels fill
+ * the tail and launch gap of the other's.  lanes = -1 restores the default (2 for a batch
+ * of one 2D shape, else 1: the groups of a batch of several shapes already overlap on
+ * their own streams); 1 turns lanes off; at most 64, and never more than a group's
+ * trajectories.  1D groups and profiled steps always run as one lane.  The split changes
+ * no result bit.  Errors: GPE_EINVAL (lanes not -1 or 1..64). */
+gpe_status gpe_batch_set_lanes(gpe_batch* batch, int32_t lanes);
+/* Lanes the group of trajectory ``traj`` is stepped in now.  Errors: GPE_EINVAL. */
+gpe_status gpe_batch_get_lanes(const gpe_batch* batch, int32_t traj, int32_t* lanes);
+
 /* Test hook for the bounded waits (failure handling; the paper has no counterpart).  Sets
  * how many times the first wait of each block of the x pass and of the tensor-map
  * strided pass may poll its copy barrier before the wait counts as expired: -1 restores

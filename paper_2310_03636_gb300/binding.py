@@ -75,6 +75,8 @@ def _load():
         "gpe_batch_set_tiles": ([vp, i32, i32, i32], ctypes.c_int),
         "gpe_batch_set_xpass_threads": ([vp, i32, i32], ctypes.c_int),
         "gpe_batch_get_xpass_threads": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "gpe_batch_set_lanes": ([vp, i32], ctypes.c_int),
+        "gpe_batch_get_lanes": ([vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "gpe_batch_set_mean_field": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),
         "gpe_check_sincos": ([vp, vp, i64, vp], ctypes.c_int),
         "gpe_fma_rate": ([i32, i64, ctypes.POINTER(dbl), vp], ctypes.c_int),
@@ -375,6 +377,16 @@ class GPEBatch:
         t = ctypes.c_int32()
         _check(LIB.gpe_batch_get_xpass_threads(self.h, int(traj), ctypes.byref(t)))
         return int(t.value)
+
+    def set_lanes(self, lanes=-1):
+        """Trajectory lanes per 2D/3D shape group (-1: the default, 1: off, at most 64)."""
+        _check(LIB.gpe_batch_set_lanes(self.h, int(lanes)))
+
+    def lanes(self, traj=0):
+        """Lanes the shape group of trajectory traj is stepped in."""
+        n = ctypes.c_int32()
+        _check(LIB.gpe_batch_get_lanes(self.h, int(traj), ctypes.byref(n)))
+        return int(n.value)
 
     def tiles(self, traj=0):
         """(cols_y, cols_z, tuned) of the column passes of trajectory traj's group."""

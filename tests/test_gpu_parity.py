@@ -117,6 +117,71 @@ def test_propagation_fp32_3d_200_steps(B):
     b.close()
 
 
+@pytest.mark.parametrize("dtype,shape,steps,tol", [
+    ("c64", (1024, 1024), 20, 1e-4),      # largest x and y extents
+    ("c128", (1024, 1024), 8, 1e-11),
+    ("c64", (64, 64, 1024), 6, 1e-4),     # largest z extent (tensor-map z pass)
+    ("c64", (1024, 64, 64), 6, 1e-4),     # largest x extent in 3D
+])
+def test_maximum_grids_vs_oracle(B, dtype, shape, steps, tol):
+    """The largest extent each pass accepts (1024 points per axis), one trajectory, element
+    by element against the oracle."""
+    seed, dt = 31, 0.02
+    b = B.GPEBatch(shape, 1, dtype, C0, C1, Q, dt)
+    b.init_noise(seed, MEAN, 0.5)
+    b.step(steps)
+    assert b.sync_status() == B.GPE_OK
+    gpu = b.psi.cpu().numpy().astype(np.complex128)
+    ref = run_oracle(oracle_initial(shape, 1, seed), dt, steps, len(shape))
+    assert rel_l2_per_comp(gpu, ref) <= tol
+    b.close()
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("shape", [(256,), (64, 128), (64, 64, 64)])
+def test_single_component_states_keep_closed_form(B, dtype, shape):
+    """Degenerate states of Eq. (GPE) with a closed form: a uniform field in one component
+    only.  Then a = psi_-1^* psi_0 = 0 and b = psi_0^* psi_1 = 0, so the spin-mixing step is
+    the identity and the empty components stay exactly zero, and the occupied one turns at
+    its mean-field rate: f_0 = (c0 + c1) rho - c1 |psi_0|^2 = c0 rho for m = 0, and
+    f_1 = q + (c0 + c1) rho - 2 c1 |psi_-1|^2 = q + (c0 + c1) rho for m = +1 (kinetic factor 1:
+    only the k = 0 mode is occupied).  The rotation integrator must agree."""
+    dt, steps, rho = 0.02, 200, 1.3
+    tol = 2e-5 if dtype == "c64" else 1e-12
+    n = int(np.prod(shape))
+    for occ, rate in ((1, C0 * rho), (0, Q + (C0 + C1) * rho)):
+        for integrator in (0, 1):
+            b = B.GPEBatch(shape, 2, dtype, C0, C1, Q, dt)
+            b.set_integrator(integrator)
+            psi = torch.zeros_like(b.psi)
+            psi[:, occ] = math.sqrt(rho)
+            b.psi.copy_(psi)
+            b.step(steps)
+            assert b.sync_status() == B.GPE_OK
+            out = b.psi.cpu().numpy().astype(np.complex128)
+            empty = [m for m in range(3) if m != occ]
+            assert np.all(out[:, empty] == 0), "empty components must stay exactly zero"
+            want = math.sqrt(rho) * np.exp(-1j * rate * dt * steps)
+            err = np.abs(out[:, occ].reshape(2, n) - want).max() / math.sqrt(rho)
+            assert err <= tol, (occ, integrator, err)
+            b.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("c64", 1e-4), ("c128", 1e-11)])
+def test_no_spin_coupling(B, dtype, tol):
+    """c1 = 0: the spin-mixing step has a zero coupling (its series coefficients at u = 0) and
+    the D step loses its spin terms; noisy fields against the oracle with the same c1."""
+    shape, ntraj, steps, dt, seed = (64, 128), 2, 100, 0.02, 5
+    b = B.GPEBatch(shape, ntraj, dtype, C0, 0.0, Q, dt)
+    b.init_noise(seed, MEAN, 0.5)
+    b.step(steps)
+    assert b.sync_status() == B.GPE_OK
+    gpu = b.psi.cpu().numpy().astype(np.complex128)
+    ref = run_oracle(oracle_initial(shape, ntraj, seed), dt, steps, 2, c1=0.0)
+    assert rel_l2_per_comp(gpu, ref) <= tol
+    b.close()
+
+
 @pytest.mark.parametrize("shape", [(64, 128), (32 * 4, 512)])
 def test_fp32_kinetic_angles_beyond_half_pi(B, shape):
     """dt and dx with kinetic phases dt k^2/2 up to 2 rad at the largest k: the tables then
@@ -348,6 +413,9 @@ def test_zero_steps_is_noop(B):
 
 def test_invalid_arguments(B):
     psi = torch.zeros((3, 64, 64), dtype=torch.complex64, device="cuda")
+    with pytest.raises(B.GPEError) as e:      # an empty batch
+        B.gpe_batch_create([], B.GPE_C64, 1, -0.1, 0.09, 0.02)
+    assert e.value.status == B.GPE_EINVAL
     with pytest.raises(B.GPEError) as e:
         B.gpe_batch_create([((64, 60), 1.0, psi)], B.GPE_C64, 1, -0.1, 0.09, 0.02)
     assert e.value.status == B.GPE_EINVAL
@@ -607,4 +675,69 @@ def test_every_xpass_block_size_gives_the_same_bits(B, shape, ntraj):
     with pytest.raises(B.GPEError) as ei:
         b.set_xpass_threads(128)
     assert ei.value.status == B.GPE_EUNSUPPORTED
+    b.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_trajectory_lanes_change_no_bit(B, graph):
+    """Splitting each 2D/3D shape group into trajectory lanes on their own streams
+    (gpe_batch_set_lanes) changes no result bit: a uniform 2D batch, a 3D batch, a ragged
+    mix with a 1D group (always one lane) and a 2D group whose fields are not back to back
+    (pointer tables instead of tensor maps), direct launches and graph replay."""
+    cases = [((128, 128), 5), ((64, 64, 64), 3)]
+    for shape, ntraj in cases:
+        out = {}
+        for lanes in (1, 2, 3, 64):
+            b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, 0.02)
+            b.set_graph(graph)
+            assert b.lanes(0) == (2 if len(shape) == 2 else 1)   # the default
+            b.set_lanes(lanes)
+            assert b.lanes(0) == min(lanes, ntraj)
+            b.init_noise(13, MEAN, 0.5)
+            b.step(4)
+            b.step(3)
+            assert b.sync_status() == B.GPE_OK
+            out[lanes] = b.psi.cpu().numpy()
+            b.close()
+        for lanes, v in out.items():
+            np.testing.assert_array_equal(v, out[1], err_msg=f"{shape} lanes={lanes}")
+    shapes = [(1024,), (128, 128), (1024,), (128, 128), (128, 128)]
+    ragged = {}
+    for lanes in (1, 2, -1):
+        b = B.GPEBatch(list(shapes), dtype="c64", dt=0.02)
+        b.set_graph(graph)
+        b.set_lanes(lanes)
+        assert b.lanes(0) == 1 and b.lanes(1) == (1 if lanes == -1 else lanes)
+        b.init_noise(29, MEAN, 0.5)
+        b.step(6)
+        assert b.sync_status() == B.GPE_OK
+        ragged[lanes] = [p.cpu().clone() for p in b.psi]
+        b.close()
+    for lanes, v in ragged.items():
+        for a, c in zip(v, ragged[1]):
+            assert torch.equal(a, c), f"ragged lanes={lanes}"
+    # three 2D trajectories in separate allocations (not back to back)
+    noncontig = {}
+    for lanes in (1, 2, 3):
+        fields = [torch.zeros((3, 128, 128), dtype=torch.complex64, device="cuda") for _ in range(3)]
+        pad = [torch.zeros(64, device="cuda") for _ in range(3)]   # keep the allocations apart
+        h = B.gpe_batch_create([((128, 128), 1.0, f) for f in fields], B.GPE_C64, C0, C1, Q, 0.02)
+        try:
+            B._check(B.LIB.gpe_batch_set_graph(h, 1 if graph else 0))
+            B._check(B.LIB.gpe_batch_set_lanes(h, lanes))
+            B.tw_init_noise(h, 31, MEAN, 0.5)
+            B.gpe_step_batch(h, 5)
+            assert B.gpe_sync_status(h) == B.GPE_OK
+            noncontig[lanes] = [f.cpu().clone() for f in fields]
+        finally:
+            B.gpe_batch_destroy(h)
+        del pad
+    for lanes, v in noncontig.items():
+        for a, c in zip(v, noncontig[1]):
+            assert torch.equal(a, c), f"separate allocations lanes={lanes}"
+    b = B.GPEBatch((64, 64), 2, "c64")
+    for bad in (0, -2, 65):
+        with pytest.raises(B.GPEError) as ei:
+            b.set_lanes(bad)
+        assert ei.value.status == B.GPE_EINVAL
     b.close()
