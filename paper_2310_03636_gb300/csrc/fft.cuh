@@ -108,13 +108,18 @@ template <int S, int DIR> struct Dft<4, S, DIR> {
     }
 };
 
-// R = R1 * R2: n = R2 n1 + n2, k = k1 + R1 k2.
+// R = R1 * R2: n = R2 n1 + n2, k = k1 + R1 k2.  The first layer is R2 DFTs of size R1 on
+// the groups {n2, n2 + R2, ...}; ``rest`` is everything after it, so a caller may rotate
+// and transform one group at a time (the same operations on every element).
 template <int R, int S, int DIR> struct Dft {
     static constexpr int R1 = (R == 8) ? 2 : 4;
     static constexpr int R2 = R / R1;
     template <typename V> __device__ __forceinline__ static void run(V* v) {
 #pragma unroll
         for (int n2 = 0; n2 < R2; ++n2) Dft<R1, R2 * S, DIR>::run(v + n2 * S);
+        rest(v);
+    }
+    template <typename V> __device__ __forceinline__ static void rest(V* v) {
 #pragma unroll
         for (int k1 = 1; k1 < R1; ++k1)
 #pragma unroll

@@ -1,5 +1,6 @@
 // Resident 1D kernel: the whole trajectory on chip for all steps.
 #include "prop_kernels.cuh"
+#include "res1d_tmem.cuh"
 
 namespace gpe {
 
@@ -20,7 +21,8 @@ namespace gpe {
 //
 // The stage twiddles of the first twiddled stage (R - 1 rows of R entries: 3.8 KB at
 // R = 16) sit in shared memory beside the field, tws_s; the later stages' entries, and the
-// phases, are read through L1 (tws).
+// phases, are read through L1 (tws), except at N = 4096 in FP32, where every thread keeps
+// its own last-stage twiddles and full-step phases in tensor memory (res1d_tmem.cuh).
 template <typename T, int N, int R>
 constexpr int res1d_tw_split() {
     using P = FftPlan<N, R>;
@@ -45,6 +47,34 @@ __device__ __forceinline__ void kinetic_resident(cplx<T>* const (&buf)[3], const
 #pragma unroll
         for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
         fft_pencil_split<N, R, +1, 1, SY, SPLIT>(v, b1, tws_s, tws, t);
+#pragma unroll
+        for (int m = 0; m < R; ++m) buf[c][spad(t + m * TP)] = v[0][m];
+    }
+    __syncthreads();
+}
+
+// kinetic_resident for the tensor-memory variant: the transforms of fft4096_tmem and, with
+// ph_tmem, the phases from tensor memory.
+template <int N, int R, Sync SY>
+__device__ __forceinline__ void kinetic_resident_tmem(float2* const (&buf)[3], const float4* tws_s,
+                                                      const float4* __restrict__ ph, bool ph_tmem, uint32_t ta,
+                                                      int t) {
+    constexpr int TP = N / R;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        float2 v[1][R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[0][m] = buf[c][spad(t + m * TP)];
+        pencil_sync<SY>();
+        float2* const b1[1] = {buf[c]};
+        fft4096_tmem<-1>(v, b1, tws_s, ta, t);
+        if (ph_tmem) {
+            phase4096_tmem(v[0], ta);
+        } else {
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
+        }
+        fft4096_tmem<+1>(v, b1, tws_s, ta, t);
 #pragma unroll
         for (int m = 0; m < R; ++m) buf[c][spad(t + m * TP)] = v[0][m];
     }
@@ -89,12 +119,24 @@ k_resident1d(const Res1DArgs<T> a) {
     const int tid = threadIdx.x, grp = tid / TP, t = tid % TP;
     V* g = a.ptrs[blockIdx.x];
     V* const buf[3] = {sm, sm + LD, sm + 2 * LD};
+    constexpr bool TM = res1d_tmem<T, N, R, G>();
+    __shared__ uint32_t tslot;
+    uint32_t tbase = 0, ta = 0;
+    if constexpr (TM) {
+        tbase = res1d_tmem_open(&tslot);
+        ta = res1d_tmem_row(tbase);
+        res1d_tmem_fill(ta, tws, a.ph_full, 1, 0, t);
+    }
     copy_table(tws_s, tws, res1d_tw_split<T, N, R>());
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
         for (int i = tid; i < N; i += NT) buf[c][spad(i)] = g[c * N + i];
     __syncthreads();
-    kinetic_resident<T, N, R, G, SY>(buf, tws_s, tws, a.ph_half, t, grp);
+    auto kinetic = [&](const twel<T>* ph, bool ph_full) {
+        if constexpr (TM) kinetic_resident_tmem<N, R, SY>(buf, tws_s, ph, ph_full, ta, t);
+        else kinetic_resident<T, N, R, G, SY>(buf, tws_s, tws, ph, t, grp);
+    };
+    kinetic(a.ph_half, false);
     LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
@@ -112,11 +154,13 @@ k_resident1d(const Res1DArgs<T> a) {
             }
         }
         __syncthreads();
-        kinetic_resident<T, N, R, G, SY>(buf, tws_s, tws, (s == a.nsteps - 1) ? a.ph_half : a.ph_full, t, grp);
+        const bool last = s == a.nsteps - 1;
+        kinetic(last ? a.ph_half : a.ph_full, !last);
     }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
         for (int i = tid; i < N; i += NT) g[c * N + i] = buf[c][spad(i)];
+    if constexpr (TM) res1d_tmem_close(tbase);
 }
 
 template <typename T, int N>

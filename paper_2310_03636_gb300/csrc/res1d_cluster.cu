@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include "prop_kernels.cuh"
+#include "res1d_tmem.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -54,7 +55,9 @@ constexpr int res1d_cluster_blocks() {
 // stays small (the form holding all three components in registers was instruction-fetch
 // bound).  Per component: gather the radix-C inputs from every block, barrier (all reads
 // done before the slice is overwritten), local transforms and phase, publish z_rank,
-// barrier, gather the inverse radix-C step, barrier, store the new slice.
+// barrier, gather the inverse radix-C step, barrier, store the new slice.  FP32 slices of
+// 4096 points keep each thread's last-stage twiddles and full-step phases in tensor memory
+// (res1d_tmem.cuh), as the resident kernel does.
 template <typename T, int M, int R, int C>
 __global__ void __launch_bounds__(M / R, res1d_cluster_blocks<T, M, R>())
 k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, const twel<T>* __restrict__ wn) {
@@ -74,12 +77,20 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
     const V* rbuf[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) rbuf[c] = cl.map_shared_rank(buf, c);
+    constexpr bool TM = res1d_tmem<T, M, R, 1>();
+    __shared__ uint32_t tslot;
+    uint32_t tbase = 0, ta = 0;
+    if constexpr (TM) {
+        tbase = res1d_tmem_open(&tslot);
+        ta = res1d_tmem_row(tbase);
+        res1d_tmem_fill(ta, tw_local, a.ph_full, C, rank, t);
+    }
     copy_table(tws_s, tw_local, SPLIT);
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
         for (int i = t; i < M; i += TP) buf[c * LD + spad(i)] = g[c * N + i];
 
-    auto kinetic = [&](const twel<T>* __restrict__ ph) {
+    auto kinetic = [&](const twel<T>* __restrict__ ph, bool ph_tmem) {
         cl.sync();   // every block's slices are final (loads, local step) before they are read
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {
@@ -94,10 +105,21 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
             }
             cl.sync();   // all reads of component c done before it is overwritten
             V* const fb[1] = {buf + c * LD};
-            fft_pencil_split<M, R, -1, 1, Sync::Block, SPLIT>(v, fb, tws_s, tw_local, t);
+            if constexpr (TM) {
+                fft4096_tmem<-1>(v, fb, tws_s, ta, t);
+                if (ph_tmem) {
+                    phase4096_tmem(v[0], ta);
+                } else {
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[C * (t + m * TP) + rank]);
-            fft_pencil_split<M, R, +1, 1, Sync::Block, SPLIT>(v, fb, tws_s, tw_local, t);
+                    for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[C * (t + m * TP) + rank]);
+                }
+                fft4096_tmem<+1>(v, fb, tws_s, ta, t);
+            } else {
+                fft_pencil_split<M, R, -1, 1, Sync::Block, SPLIT>(v, fb, tws_s, tw_local, t);
+#pragma unroll
+                for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[C * (t + m * TP) + rank]);
+                fft_pencil_split<M, R, +1, 1, Sync::Block, SPLIT>(v, fb, tws_s, tw_local, t);
+            }
 #pragma unroll
             for (int m = 0; m < R; ++m) buf[c * LD + spad(t + m * TP)] = v[0][m];
             cl.sync();   // z_rank published
@@ -119,7 +141,7 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
         __syncthreads();
     };
 
-    kinetic(a.ph_half);
+    kinetic(a.ph_half, false);
     LocalCoef<T> coef{a.c0, a.c1, (T)a.q_const, a.dt, a.kind};
     for (int64_t s = 0; s < a.nsteps; ++s) {
         coef.q = (T)q_at(a.t0 + ((double)s + 0.5) * a.dt_d, a.q_const, a.knots, a.n_knots, a.t_end);
@@ -136,11 +158,13 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
                 buf[2 * LD + k] = pm;
             }
         }
-        kinetic(s == a.nsteps - 1 ? a.ph_half : a.ph_full);
+        const bool last = s == a.nsteps - 1;
+        kinetic(last ? a.ph_half : a.ph_full, !last);
     }
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
         for (int i = t; i < M; i += TP) g[c * N + i] = buf[c * LD + spad(i)];
+    if constexpr (TM) res1d_tmem_close(tbase);
 }
 
 template <typename T, int M, int R, int C>

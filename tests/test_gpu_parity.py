@@ -87,7 +87,8 @@ def test_propagation_fp64(B, shape, ntraj, dt, steps):
     b.close()
 
 
-@pytest.mark.parametrize("shape,ntraj,steps", [((256,), 2, 200), ((128, 128), 4, 200), ((64, 64, 64), 1, 50)])
+@pytest.mark.parametrize("shape,ntraj,steps", [((256,), 2, 200), ((4096,), 2, 200), ((128, 128), 4, 200),
+                                         ((64, 64, 64), 1, 50)])
 def test_propagation_fp32(B, shape, ntraj, steps):
     seed, dt = 77, 0.02
     b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, dt)
@@ -741,3 +742,23 @@ def test_trajectory_lanes_change_no_bit(B, graph):
             b.set_lanes(bad)
         assert ei.value.status == B.GPE_EINVAL
     b.close()
+
+
+def test_resident_4096_fp32_split_calls(B):
+    """The paper's 1D grid in FP32 (resident kernel with its last-stage twiddles and
+    full-step phases in tensor memory, the half-step phases of a call's first and last step
+    read from the table): calls of 1, 2, 0 and 37 steps, and one call of 40, against the
+    oracle's single run."""
+    shape, ntraj, dt, seed = (4096,), 3, 0.02, 19
+    outs = []
+    for chunks in ((1, 2, 0, 37), (40,)):
+        b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, dt)
+        b.init_noise(seed, MEAN, 0.5)
+        for n in chunks:
+            b.step(n)
+        assert b.sync_status() == B.GPE_OK
+        outs.append(b.psi.cpu().numpy())
+        b.close()
+    ref = run_oracle(oracle_initial(shape, ntraj, seed), dt, 40, 1)
+    assert rel_l2_per_comp(outs[0].astype(np.complex128), ref) <= 1e-4
+    assert rel_l2_per_comp(outs[1].astype(np.complex128), ref) <= 1e-4
