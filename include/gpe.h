@@ -220,6 +220,14 @@ gpe_status gpe_batch_set_wait_limit(gpe_batch* batch, int64_t first_wait_polls);
  * Always returns GPE_OK. */
 gpe_status gpe_debug_fail_alloc(int64_t after);
 
+/* Test hook for the table placement (the paper has no counterpart): mode 1 (the default)
+ * lets the kernels built for it keep each thread's stage twiddles and kinetic phases in
+ * its own row of tensor memory (the resident and cluster 1D kernels at 4096-point FP32
+ * transforms); mode 0 makes them read those tables through L1.  Both give the same result bits.  Process-wide, read at
+ * each launch (graphs captured earlier keep the kernels they captured).  Errors:
+ * GPE_EINVAL (mode not 0 or 1). */
+gpe_status gpe_debug_table_memory(int32_t mode);
+
 /* Tile autotuner of the kinetic passes (the paper prescribes none; the choices change no
  * result bit).  Enabled by default: the first gpe_step_batch call of an FP32 batch times,
  * per 2D/3D shape group, on a zero-filled scratch batch of the group's shape (at most

@@ -67,6 +67,7 @@ def _load():
         "gpe_batch_set_graph": ([vp, i32], ctypes.c_int),
         "gpe_batch_set_wait_limit": ([vp, i64], ctypes.c_int),
         "gpe_debug_fail_alloc": ([i64], ctypes.c_int),
+        "gpe_debug_table_memory": ([i32], ctypes.c_int),
         "gpe_batch_set_integrator": ([vp, i32], ctypes.c_int),
         "gpe_batch_set_traj_base": ([vp, i64], ctypes.c_int),
         "gpe_batch_set_potential": ([vp, ctypes.POINTER(i32), vp], ctypes.c_int),

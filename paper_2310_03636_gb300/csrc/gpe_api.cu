@@ -49,6 +49,7 @@ std::atomic<int64_t> g_launches{0};
 // Allocation-failure test hook: number of device allocations still allowed to succeed
 // before one fails (-1: off).
 std::atomic<int64_t> g_alloc_fail_after{-1};
+std::atomic<int> g_table_tmem{1};   // gpe_debug_table_memory
 
 constexpr int kProfKinds = 6;
 
@@ -70,6 +71,8 @@ struct Profiler {
 }  // namespace
 
 void gpe::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+bool gpe::tables_in_tmem() { return g_table_tmem.load() != 0; }
 
 cudaError_t gpe::device_malloc(void** p, size_t bytes) {
     int64_t left = g_alloc_fail_after.load();
@@ -1338,6 +1341,13 @@ gpe_status gpe_batch_set_wait_limit(gpe_batch* b, int64_t first_wait_polls) {
 
 gpe_status gpe_debug_fail_alloc(int64_t after) {
     g_alloc_fail_after.store(after < 0 ? -1 : after);
+    return GPE_OK;
+}
+
+gpe_status gpe_debug_table_memory(int32_t mode) {
+    g_err.clear();
+    if (mode != 0 && mode != 1) return fail(GPE_EINVAL, "table memory mode must be 0 or 1");
+    g_table_tmem.store(mode);
     return GPE_OK;
 }
 

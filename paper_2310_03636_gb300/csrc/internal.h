@@ -113,6 +113,10 @@ void set_last_error(const char* msg);
 // (gpe_debug_fail_alloc) can make one fail as if the device were out of memory.
 cudaError_t device_malloc(void** p, size_t bytes);
 
+// Whether kernels built for it may keep per-thread tables in tensor memory (the test hook
+// gpe_debug_table_memory; on by default).
+bool tables_in_tmem();
+
 template <typename T> int xpass_max_n();
 template <typename T> int colpass_max_n();
 template <typename T> int resident1d_max_n();

@@ -104,7 +104,7 @@ constexpr int res1d_blocks() {
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
-template <typename T, int N, int R, int G>
+template <typename T, int N, int R, int G, bool TMW = true>
 __global__ void __launch_bounds__(G * (N / R), res1d_blocks<T, N, G>())
 k_resident1d(const Res1DArgs<T> a) {
     using V = cplx<T>;
@@ -119,7 +119,7 @@ k_resident1d(const Res1DArgs<T> a) {
     const int tid = threadIdx.x, grp = tid / TP, t = tid % TP;
     V* g = a.ptrs[blockIdx.x];
     V* const buf[3] = {sm, sm + LD, sm + 2 * LD};
-    constexpr bool TM = res1d_tmem<T, N, R, G>();
+    constexpr bool TM = TMW && res1d_tmem<T, N, R, G>();
     __shared__ uint32_t tslot;
     uint32_t tbase = 0, ta = 0;
     if constexpr (TM) {
@@ -167,6 +167,10 @@ template <typename T, int N>
 cudaError_t resident1d_n(const Res1DArgs<T>& a, cudaStream_t s) {
     constexpr int R = Tune<T>::kResR(N);
     constexpr int G = res1d_groups<T, N>();
+    if constexpr (res1d_tmem<T, N, R, G>()) {
+        if (!tables_in_tmem())
+            return launch_with_smem(k_resident1d<T, N, R, G, false>, a.ntraj, G * (N / R), res1d_smem<T, N, R>(), s, &a);
+    }
     return launch_with_smem(k_resident1d<T, N, R, G>, a.ntraj, G * (N / R), res1d_smem<T, N, R>(), s, &a);
 }
 

@@ -58,7 +58,7 @@ constexpr int res1d_cluster_blocks() {
 // barrier, gather the inverse radix-C step, barrier, store the new slice.  FP32 slices of
 // 4096 points keep each thread's last-stage twiddles and full-step phases in tensor memory
 // (res1d_tmem.cuh), as the resident kernel does.
-template <typename T, int M, int R, int C>
+template <typename T, int M, int R, int C, bool TMW = true>
 __global__ void __launch_bounds__(M / R, res1d_cluster_blocks<T, M, R>())
 k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, const twel<T>* __restrict__ wn) {
     using V = cplx<T>;
@@ -77,7 +77,7 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
     const V* rbuf[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) rbuf[c] = cl.map_shared_rank(buf, c);
-    constexpr bool TM = res1d_tmem<T, M, R, 1>();
+    constexpr bool TM = TMW && res1d_tmem<T, M, R, 1>();
     __shared__ uint32_t tslot;
     uint32_t tbase = 0, ta = 0;
     if constexpr (TM) {
@@ -169,7 +169,10 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
 
 template <typename T, int M, int R, int C>
 cudaError_t res1d_cluster_n(const Res1DArgs<T>& a, const twel<T>* tw_local, const twel<T>* wn, cudaStream_t s) {
-    auto kern = k_res1d_cluster<T, M, R, C>;
+    auto kern = k_res1d_cluster<T, M, R, C, true>;
+    if constexpr (res1d_tmem<T, M, R, 1>()) {
+        if (!tables_in_tmem()) kern = k_res1d_cluster<T, M, R, C, false>;
+    }
     const size_t smem = res1d_cluster_smem<T, M, R>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

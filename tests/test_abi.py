@@ -59,3 +59,9 @@ def test_argument_errors_without_gpu(lib):
     assert lib.gpe_fma_rate(ctypes.c_int32(0), ctypes.c_int64(16), None, None) == 1
     lib.gpe_batch_set_tiles.restype = ctypes.c_int
     assert lib.gpe_batch_set_tiles(None, 0, 4, 0) == 1
+    lib.gpe_batch_set_lanes.restype = ctypes.c_int
+    assert lib.gpe_batch_set_lanes(None, 2) == 1
+    lib.gpe_debug_table_memory.restype = ctypes.c_int
+    assert lib.gpe_debug_table_memory(ctypes.c_int32(2)) == 1
+    assert lib.gpe_debug_table_memory(ctypes.c_int32(-1)) == 1
+    assert lib.gpe_debug_table_memory(ctypes.c_int32(1)) == 0

@@ -762,3 +762,25 @@ def test_resident_4096_fp32_split_calls(B):
     ref = run_oracle(oracle_initial(shape, ntraj, seed), dt, 40, 1)
     assert rel_l2_per_comp(outs[0].astype(np.complex128), ref) <= 1e-4
     assert rel_l2_per_comp(outs[1].astype(np.complex128), ref) <= 1e-4
+
+
+@pytest.mark.parametrize("shape,ntraj,steps", [((4096,), 3, 30), ((4096,), 2, 1), ((8192,), 2, 20),
+                                               ((16384,), 1, 12), ((32768,), 1, 5)])
+def test_table_memory_forms_give_the_same_bits(B, shape, ntraj, steps):
+    """The 1D kernels that keep each thread's last-stage twiddles and full-step phases in
+    tensor memory (resident at 4096 points, cluster slices of 4096; FP32) give the fields of
+    the form that reads them through L1 (gpe_debug_table_memory(0)) bit for bit."""
+    outs = {}
+    try:
+        for mode in (1, 0):
+            B._check(B.LIB.gpe_debug_table_memory(mode))
+            b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, 0.02)
+            b.init_noise(23, MEAN, 0.5)
+            b.step(steps)
+            b.step(2)
+            assert b.sync_status() == B.GPE_OK
+            outs[mode] = b.psi.cpu().numpy()
+            b.close()
+    finally:
+        B._check(B.LIB.gpe_debug_table_memory(1))
+    np.testing.assert_array_equal(outs[1].view(np.uint32), outs[0].view(np.uint32))
