@@ -470,10 +470,13 @@ def run_ours(args):
 def ncu_case():
     """Short run of the benchmark workload for ncu captures: noise, 4 steps, one observables call.
     The tile autotuner is off here so that the captured launches are the workload's own
-    (the default width at 512 is the one the tuner keeps there; the bench line reports it)."""
+    (the default width at 512 is the one the tuner keeps there; the bench line reports it),
+    and the batch runs as one trajectory lane, so that each captured launch covers the whole
+    batch like the per-kernel timings of the bench line."""
     from paper_2310_03636_gb300 import binding as B
     b = B.GPEBatch(WL.shape, WL.ntraj, "c64", WL.c0, WL.c1, WL.q, WL.dt, dx=WL.dx)
     b.set_autotune(False)
+    b.set_lanes(1)
     b.init_noise(W.SEED_BASE, WL.mean_spinor(), WL.noise_per_mode)
     b.step(4)
     acc = b.new_accumulator(1)
