@@ -80,3 +80,26 @@ def test_coarsening_driver_small(B):
     assert arr["S_perp"][-1][kq].mean() > 10 * arr["S_perp"][0][kq].mean()
     for key in ("beta_moment", "beta_collapse"):
         assert np.isfinite(res[key])
+
+
+def test_sweep3d_driver_against_oracle(B):
+    """The 3D quench-sweep driver (sweep3d.run_one) in FP64 on a small grid: its per-sample
+    totals and drifts of N, F_z and E equal those of the oracle's run of the same steps
+    (diagnostics of the oracle's fields at the same sample times, the same summary)."""
+    from oracle.philox import tw_noise
+    from paper_2310_03636_gb300 import sweep3d
+    n, ntraj, steps, every, q, dt, seed = 64, 1, 40, 20, 0.15, 0.02, 20231005
+    r = sweep3d.run_one(n, ntraj, q, steps, every, dt=dt, seed=seed, dtype="c128")
+    psi = np.stack([tw_noise((n, n, n), seed, t, 0.5, 1.0) for t in range(ntraj)])
+    psi[:, 1] += 1.0
+    p = torch.as_tensor(psi)
+    recs = [O.diagnostics(p, 1.0, 1.0, -0.1, q, 3).numpy()]
+    for _ in range(steps // every):
+        p = O.propagate(p, dt, every, 1.0, -0.1, q, 1.0, 3)
+        recs.append(O.diagnostics(p, 1.0, 1.0, -0.1, q, 3).numpy())
+    ref = sweep3d.drift_summary(np.stack(recs))
+    for key in ("N", "F_z", "E"):
+        np.testing.assert_allclose(r[key], ref[key], rtol=1e-10, atol=1e-9 * abs(ref["N"][0]), err_msg=key)
+    for key in ("max_rel_dN", "max_rel_dFz", "max_rel_dE"):
+        np.testing.assert_allclose(r[key], ref[key], rtol=1e-3, atol=1e-12, err_msg=key)
+    assert max(r["max_rel_dN"]) < 1e-12
