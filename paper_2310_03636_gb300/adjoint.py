@@ -61,17 +61,10 @@ class SpinSFLoss(torch.autograd.Function):
         lam.mul_(g_loss.to(device="cuda", dtype=torch.float64).item())
         dq = torch.zeros(max(1, ctx.nknots), dtype=torch.float64, device="cuda")
         bounds = [n for n, _ in ctx.ckpts] + [cfg.nsteps]
+        states = torch.empty((cfg.checkpoint_every,) + tuple(psi.shape), dtype=psi.dtype, device=psi.device)
         for seg in range(len(ctx.ckpts) - 1, -1, -1):
             n0, ck = ctx.ckpts[seg]
-            n1 = bounds[seg + 1]
-            psi.copy_(ck)
-            b.set_step(n0)
-            states = [ck]
-            for _ in range(n0, n1 - 1):
-                b.step(1)
-                states.append(psi.clone())
-            for n in range(n1 - 1, n0 - 1, -1):
-                B.gpe_adjoint_step(b.h, states[n - n0], lam, n, dq)
+            B.gpe_adjoint_segment(b.h, ck, states, n0, bounds[seg + 1] - n0, lam, dq)
         st = b.sync_status()
         if st != B.GPE_OK:
             raise B.GPEError(st, "device status after the adjoint sweep")

@@ -62,6 +62,7 @@ def _load():
         "gpe_profile_enable": ([vp, i32], ctypes.c_int),
         "gpe_profile_read": ([vp, pd, ctypes.POINTER(i64)], ctypes.c_int),
         "gpe_adjoint_step": ([vp, vp, vp, i64, vp, vp], ctypes.c_int),
+        "gpe_adjoint_segment": ([vp, vp, vp, i64, i64, vp, vp, vp], ctypes.c_int),
         "gpe_sf_band_loss": ([vp, vp, dbl, dbl, vp, vp, vp], ctypes.c_int),
         "gpe_launch_count": ([], i64),
         "gpe_batch_set_graph": ([vp, i32], ctypes.c_int),
@@ -186,6 +187,18 @@ def gpe_adjoint_step(h, psi_step_in, lam, step_index, dLdq, stream=None):
     assert dLdq.dtype == torch.float64 and dLdq.is_cuda
     _check(LIB.gpe_adjoint_step(h, ctypes.c_void_p(psi_step_in.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
                                 int(step_index), ctypes.c_void_p(dLdq.data_ptr()), _stream(stream)))
+
+
+def gpe_adjoint_segment(h, psi_ckpt, states, n0, nseg, lam, dLdq, stream=None):
+    """psi_ckpt, lam: contiguous (ntraj, 3, *shape) complex CUDA tensors; states: contiguous
+    CUDA tensor of at least nseg such fields; dLdq: float64 CUDA."""
+    for t in (psi_ckpt, states, lam):
+        assert t.is_cuda and t.is_contiguous()
+    assert states.numel() >= nseg * psi_ckpt.numel() and states.dtype == psi_ckpt.dtype
+    assert dLdq.dtype == torch.float64 and dLdq.is_cuda
+    _check(LIB.gpe_adjoint_segment(h, ctypes.c_void_p(psi_ckpt.data_ptr()), ctypes.c_void_p(states.data_ptr()),
+                                   int(n0), int(nseg), ctypes.c_void_p(lam.data_ptr()),
+                                   ctypes.c_void_p(dLdq.data_ptr()), _stream(stream)))
 
 
 def gpe_sf_band_loss(h, psi, kmin, kmax, loss, lam_out=None, stream=None):

@@ -1154,6 +1154,40 @@ gpe_status gpe_adjoint_step(gpe_batch* b, const void* psi_step_in, void* lam, in
                                : adjoint_step_t<double>(b, psi_step_in, lam, step_index, dLdq, s);
 }
 
+gpe_status gpe_adjoint_segment(gpe_batch* b, const void* psi_ckpt, void* states, int64_t n0, int64_t nseg, void* lam,
+                               double* dLdq, void* stream) {
+    g_err.clear();
+    gpe_status st = adj_check(b, psi_ckpt, lam);
+    if (st != GPE_OK) return st;
+    if (!lam || !dLdq || !states) return fail(GPE_EINVAL, "states, lam and dLdq must be non-NULL");
+    if (((uintptr_t)states & 15u) != 0) return fail(GPE_EINVAL, "states not 16-byte aligned");
+    if (b->integrator != GPE_INTEGRATOR_PAPER) return fail(GPE_EUNSUPPORTED, "the adjoint is written for the paper's local step");
+    if (n0 < 0 || nseg < 1) return fail(GPE_EINVAL, "need n0 >= 0 and nseg >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Group& g = b->groups[0];
+    const size_t fb = (b->dtype == GPE_C64 ? sizeof(float2) : sizeof(double2)) * 3 * (size_t)g.sites;
+    const size_t batch_bytes = fb * (size_t)g.ntraj;
+    // recompute: the batch's own fields step from psi_ckpt, each state copied out before its
+    // step (one copy for the whole batch when its fields are back to back)
+    const int ncopies = g.contiguous ? 1 : g.ntraj;
+    const size_t cb = g.contiguous ? batch_bytes : fb;
+    for (int i = 0; i < ncopies; ++i)
+        GPE_CK(cudaMemcpyAsync(g.hptrs[i], (const char*)psi_ckpt + i * fb, cb, cudaMemcpyDeviceToDevice, s));
+    b->step = n0;
+    for (int64_t j = 0; j < nseg; ++j) {
+        char* dst = (char*)states + (size_t)j * batch_bytes;
+        for (int i = 0; i < ncopies; ++i)
+            GPE_CK(cudaMemcpyAsync(dst + i * fb, g.hptrs[i], cb, cudaMemcpyDeviceToDevice, s));
+        if (j + 1 < nseg && (st = gpe_step_batch(b, 1, stream)) != GPE_OK) return st;
+    }
+    // reverse sweep from step n0 + nseg - 1 down to n0
+    for (int64_t j = nseg - 1; j >= 0; --j) {
+        st = gpe_adjoint_step(b, (const char*)states + (size_t)j * batch_bytes, lam, n0 + j, dLdq, stream);
+        if (st != GPE_OK) return st;
+    }
+    return GPE_OK;
+}
+
 gpe_status gpe_sf_band_loss(gpe_batch* b, const void* psi, double kmin, double kmax, double* loss, void* lam_out,
                             void* stream) {
     g_err.clear();

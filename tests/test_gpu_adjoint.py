@@ -204,3 +204,53 @@ def test_full_size_adjoint_workload(B):
     assert abs(lhs - rhs) < 1e-7 * abs(lhs)
     bp.close()
     bm.close()
+
+
+@pytest.mark.parametrize("dtype,shape,knots", [("c128", (64, 128), [0.2, 0.1, 0.05]), ("c64", (128, 128), None),
+                                               ("c64", (64, 64, 64), [0.1, 0.3])])
+def test_adjoint_segment_equals_step_by_step(B, dtype, shape, knots):
+    """gpe_adjoint_segment (recompute and reverse sweep of one checkpoint segment inside the
+    library) gives the cotangent and dL/dq of the step-by-step calls it replaces (recompute
+    with gpe_step_batch(1), then gpe_adjoint_step per step) bit for bit, and leaves the
+    batch's fields and step counter as that loop does."""
+    ntraj, dt, n0, nseg = 2, 0.03, 5, 11
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    ck = torch.as_tensor(W.random_field(shape, ntraj, seed=51, scale=0.8)).to("cuda", tdt).contiguous()
+    lam0 = torch.as_tensor(W.random_field(shape, ntraj, seed=52, scale=1.0)).to("cuda", tdt).contiguous()
+    nk = len(knots) if knots else 1
+    kw = dict(q_knots=knots, t_end=30 * dt) if knots else {}
+    res = []
+    for mode in ("loop", "segment"):
+        psi = torch.zeros_like(ck)
+        b = B.GPEBatch(shape, ntraj, dtype, C0, C1, 0.09, dt, psi=psi, **kw)
+        b.set_autotune(False)
+        lam = lam0.clone()
+        dq = torch.zeros(nk, dtype=torch.float64, device="cuda")
+        if mode == "loop":
+            psi.copy_(ck)
+            b.set_step(n0)
+            states = [ck.clone()]
+            for _ in range(nseg - 1):
+                b.step(1)
+                states.append(psi.clone())
+            for j in range(nseg - 1, -1, -1):
+                B.gpe_adjoint_step(b.h, states[j], lam, n0 + j, dq)
+        else:
+            ws = torch.empty((nseg,) + tuple(ck.shape), dtype=tdt, device="cuda")
+            B.gpe_adjoint_segment(b.h, ck, ws, n0, nseg, lam, dq)
+        assert b.sync_status() == B.GPE_OK
+        res.append((lam.cpu().numpy(), dq.cpu().numpy(), psi.cpu().numpy(), b.step_count))
+        b.close()
+    (l1, q1, p1, s1), (l2, q2, p2, s2) = res
+    np.testing.assert_array_equal(l1, l2)
+    np.testing.assert_array_equal(q1, q2)
+    np.testing.assert_array_equal(p1, p2)
+    assert s1 == s2 == n0 + nseg - 1
+    b = B.GPEBatch(shape, ntraj, dtype, C0, C1, 0.09, dt)
+    ws = torch.empty((1,) + tuple(ck.shape), dtype=tdt, device="cuda")
+    dq = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.GPEError) as ei:
+        B._check(B.LIB.gpe_adjoint_segment(b.h, ck.data_ptr(), ws.data_ptr(), 0, 0, lam0.data_ptr(),
+                                           dq.data_ptr(), None))
+    assert ei.value.status == B.GPE_EINVAL
+    b.close()
