@@ -222,8 +222,8 @@ gpe_status gpe_debug_fail_alloc(int64_t after);
 
 /* Test hook for the table placement (the paper has no counterpart): mode 1 (the default)
  * lets the kernels built for it keep each thread's stage twiddles and kinetic phases in
- * its own row of tensor memory (the resident and cluster 1D kernels at 4096-point FP32
- * transforms); mode 0 makes them read those tables through L1.  Both give the same result bits.  Process-wide, read at
+ * its own row of tensor memory (the resident 1D kernel at 2048 and 4096 points and the
+ * cluster kernel's 4096-point slices, FP32); mode 0 makes them read those tables through L1.  Both give the same result bits.  Process-wide, read at
  * each launch (graphs captured earlier keep the kernels they captured).  Errors:
  * GPE_EINVAL (mode not 0 or 1). */
 gpe_status gpe_debug_table_memory(int32_t mode);

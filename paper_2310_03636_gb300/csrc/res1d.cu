@@ -21,8 +21,8 @@ namespace gpe {
 //
 // The stage twiddles of the first twiddled stage (R - 1 rows of R entries: 3.8 KB at
 // R = 16) sit in shared memory beside the field, tws_s; the later stages' entries, and the
-// phases, are read through L1 (tws), except at N = 4096 in FP32, where every thread keeps
-// its own last-stage twiddles and full-step phases in tensor memory (res1d_tmem.cuh).
+// phases, are read through L1 (tws), except at N = 4096 and 2048 in FP32, where every thread
+// keeps its own last-stage twiddles and full-step phases in tensor memory (res1d_tmem.cuh).
 template <typename T, int N, int R>
 constexpr int res1d_tw_split() {
     using P = FftPlan<N, R>;
@@ -53,7 +53,7 @@ __device__ __forceinline__ void kinetic_resident(cplx<T>* const (&buf)[3], const
     __syncthreads();
 }
 
-// kinetic_resident for the tensor-memory variant: the transforms of fft4096_tmem and, with
+// kinetic_resident for the tensor-memory variant: the transforms of fft_tmem and, with
 // ph_tmem, the phases from tensor memory.
 template <int N, int R, Sync SY>
 __device__ __forceinline__ void kinetic_resident_tmem(float2* const (&buf)[3], const float4* tws_s,
@@ -67,14 +67,14 @@ __device__ __forceinline__ void kinetic_resident_tmem(float2* const (&buf)[3], c
         for (int m = 0; m < R; ++m) v[0][m] = buf[c][spad(t + m * TP)];
         pencil_sync<SY>();
         float2* const b1[1] = {buf[c]};
-        fft4096_tmem<-1>(v, b1, tws_s, ta, t);
+        fft_tmem<N, -1>(v, b1, tws_s, ta, t);
         if (ph_tmem) {
-            phase4096_tmem(v[0], ta);
+            phase_tmem(v[0], ta);
         } else {
 #pragma unroll
             for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[t + m * TP]);
         }
-        fft4096_tmem<+1>(v, b1, tws_s, ta, t);
+        fft_tmem<N, +1>(v, b1, tws_s, ta, t);
 #pragma unroll
         for (int m = 0; m < R; ++m) buf[c][spad(t + m * TP)] = v[0][m];
     }
@@ -123,9 +123,9 @@ k_resident1d(const Res1DArgs<T> a) {
     __shared__ uint32_t tslot;
     uint32_t tbase = 0, ta = 0;
     if constexpr (TM) {
-        tbase = res1d_tmem_open(&tslot);
+        tbase = res1d_tmem_open(&tslot, res1d_tmem_cols<N>());
         ta = res1d_tmem_row(tbase);
-        res1d_tmem_fill(ta, tws, a.ph_full, 1, 0, t);
+        res1d_tmem_fill<N>(ta, tws, a.ph_full, 1, 0, t);
     }
     copy_table(tws_s, tws, res1d_tw_split<T, N, R>());
 #pragma unroll 1
@@ -160,7 +160,7 @@ k_resident1d(const Res1DArgs<T> a) {
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
         for (int i = tid; i < N; i += NT) g[c * N + i] = buf[c][spad(i)];
-    if constexpr (TM) res1d_tmem_close(tbase);
+    if constexpr (TM) res1d_tmem_close(tbase, res1d_tmem_cols<N>());
 }
 
 template <typename T, int N>

@@ -81,9 +81,9 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
     __shared__ uint32_t tslot;
     uint32_t tbase = 0, ta = 0;
     if constexpr (TM) {
-        tbase = res1d_tmem_open(&tslot);
+        tbase = res1d_tmem_open(&tslot, res1d_tmem_cols<M>());
         ta = res1d_tmem_row(tbase);
-        res1d_tmem_fill(ta, tw_local, a.ph_full, C, rank, t);
+        res1d_tmem_fill<M>(ta, tw_local, a.ph_full, C, rank, t);
     }
     copy_table(tws_s, tw_local, SPLIT);
 #pragma unroll 1
@@ -106,14 +106,14 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
             cl.sync();   // all reads of component c done before it is overwritten
             V* const fb[1] = {buf + c * LD};
             if constexpr (TM) {
-                fft4096_tmem<-1>(v, fb, tws_s, ta, t);
+                fft_tmem<M, -1>(v, fb, tws_s, ta, t);
                 if (ph_tmem) {
-                    phase4096_tmem(v[0], ta);
+                    phase_tmem(v[0], ta);
                 } else {
 #pragma unroll
                     for (int m = 0; m < R; ++m) v[0][m] = phmul<-1>(v[0][m], ph[C * (t + m * TP) + rank]);
                 }
-                fft4096_tmem<+1>(v, fb, tws_s, ta, t);
+                fft_tmem<M, +1>(v, fb, tws_s, ta, t);
             } else {
                 fft_pencil_split<M, R, -1, 1, Sync::Block, SPLIT>(v, fb, tws_s, tw_local, t);
 #pragma unroll
@@ -164,7 +164,7 @@ k_res1d_cluster(const Res1DArgs<T> a, const twel<T>* __restrict__ tw_local, cons
 #pragma unroll 1
     for (int c = 0; c < 3; ++c)
         for (int i = t; i < M; i += TP) g[c * N + i] = buf[c * LD + spad(i)];
-    if constexpr (TM) res1d_tmem_close(tbase);
+    if constexpr (TM) res1d_tmem_close(tbase, res1d_tmem_cols<M>());
 }
 
 template <typename T, int M, int R, int C>

@@ -87,7 +87,7 @@ def test_propagation_fp64(B, shape, ntraj, dt, steps):
     b.close()
 
 
-@pytest.mark.parametrize("shape,ntraj,steps", [((256,), 2, 200), ((4096,), 2, 200), ((128, 128), 4, 200),
+@pytest.mark.parametrize("shape,ntraj,steps", [((256,), 2, 200), ((2048,), 2, 200), ((4096,), 2, 200), ((128, 128), 4, 200),
                                          ((64, 64, 64), 1, 50)])
 def test_propagation_fp32(B, shape, ntraj, steps):
     seed, dt = 77, 0.02
@@ -764,11 +764,11 @@ def test_resident_4096_fp32_split_calls(B):
     assert rel_l2_per_comp(outs[1].astype(np.complex128), ref) <= 1e-4
 
 
-@pytest.mark.parametrize("shape,ntraj,steps", [((4096,), 3, 30), ((4096,), 2, 1), ((8192,), 2, 20),
-                                               ((16384,), 1, 12), ((32768,), 1, 5)])
+@pytest.mark.parametrize("shape,ntraj,steps", [((4096,), 3, 30), ((4096,), 2, 1), ((2048,), 5, 30), ((2048,), 1, 1),
+                                               ((8192,), 2, 20), ((16384,), 1, 12), ((32768,), 1, 5)])
 def test_table_memory_forms_give_the_same_bits(B, shape, ntraj, steps):
     """The 1D kernels that keep each thread's last-stage twiddles and full-step phases in
-    tensor memory (resident at 4096 points, cluster slices of 4096; FP32) give the fields of
+    tensor memory (resident at 4096 and 2048 points, cluster slices of 4096; FP32) give the fields of
     the form that reads them through L1 (gpe_debug_table_memory(0)) bit for bit."""
     outs = {}
     try:
