@@ -179,6 +179,7 @@ struct gpe_batch {
     void* adj_phi = nullptr;        // ntraj x 3 x sites
     void* adj_W = nullptr;          // ntraj x sites
     void** adj_ptrs = nullptr;      // 3 x ntraj pointer tables
+    void* adj_phc[3] = {};          // per strided axis: conjugated half-step phase table
     double* adj_part = nullptr;     // partial sums
     int64_t adj_nparts = 0;
 };
@@ -238,6 +239,11 @@ template <> float4 tw_entry<float>(double re, double im) {
     return make_float4((float)(-std::tan(0.5 * phi)), (float)std::sin(phi), (float)s, 0.0f);
 }
 template <> double2 tw_entry<double>(double re, double im) { return make_double2(re, im); }
+
+// The conjugate of a table entry: FP32 (p, u, s) -> (-p, -u, s) (rotation by minus the
+// reduced angle, same reduction sign), FP64 (re, im) -> (re, -im); exact.
+float4 conj_entry(float4 e) { return make_float4(-e.x, -e.y, e.z, e.w); }
+double2 conj_entry(double2 e) { return make_double2(e.x, -e.y); }
 
 template <typename T>
 void phase_tables_host(int n, double dx, double dt, std::vector<twel<T>>& pf, std::vector<twel<T>>& ph) {
@@ -1018,7 +1024,34 @@ gpe_status adj_workspace(gpe_batch* b) {
     if ((s = dev_alloc(b, (void**)&b->adj_ptrs, sizeof(void*) * 3 * g.ntraj)) != GPE_OK) return s;
     if ((s = dev_alloc(b, (void**)&b->adj_part, sizeof(double) * nparts)) != GPE_OK) return s;
     b->adj_nparts = nparts;
+    // exp(+i dt k^2/4)/n for the strided axes: the half-step table with the rotation's
+    // stored values negated (exact), so that the kinetic strided pass with it performs the
+    // conjugate pass's arithmetic
+    for (int ax = 1; ax < g.ndim; ++ax) {
+        std::vector<twel<T>> pf, ph;
+        phase_tables_host<T>(g.n[ax], g.dx, b->p.dt, pf, ph);
+        for (auto& e : ph) e = conj_entry(e);
+        const size_t bytes = sizeof(twel<T>) * ph.size();
+        if ((s = dev_alloc(b, &b->adj_phc[ax], bytes)) != GPE_OK) return s;
+        GPE_CK(cudaMemcpy(b->adj_phc[ax], ph.data(), bytes, cudaMemcpyHostToDevice));
+    }
     return GPE_OK;
+}
+
+// A contiguous view of the batch's single group over the fields at ``base`` (the adjoint's
+// workspace or the caller's cotangent) for the tensor-map strided passes; with ``conj`` its
+// half-step tables are the conjugated ones.  False if the tensor maps cannot be encoded.
+template <typename T>
+bool adj_view(const gpe_batch* b, const Group& g, const void* base, bool conj, Group& v) {
+    v = g;
+    const size_t fb = sizeof(cplx<T>) * 3 * (size_t)g.sites;
+    for (int i = 0; i < g.ntraj; ++i) v.hptrs[i] = (char*)base + i * fb;
+    for (int ax = 1; ax < g.ndim; ++ax) {
+        if (v.cols[ax] <= 0) v.cols[ax] = colpass_cols<T>(g.n[ax]);
+        if (conj) v.ph_half[ax] = b->adj_phc[ax];
+    }
+    v.contiguous = encode_group_maps(v, (int)sizeof(T));
+    return v.contiguous;
 }
 
 template <typename T>
@@ -1069,27 +1102,40 @@ gpe_status adjoint_step_t(gpe_batch* b, const void* psi_in, void* lam, int64_t s
     const size_t vb = sizeof(cplx<T>);
     const int64_t tstride = (int64_t)vb * 3 * g.sites;
     GPE_CK(cudaMemcpyAsync(b->adj_phi, psi_in, tstride * g.ntraj, cudaMemcpyDeviceToDevice, s));
+    // strided passes: the tensor-map pass over contiguous views of phi and lam (the
+    // conjugate pass as the kinetic pass with conjugated tables), else pointer tables
+    Group vphi, vlam;
+    const bool tma = g.ndim >= 2 && adj_view<T>(b, g, b->adj_phi, false, vphi) && adj_view<T>(b, g, lam, true, vlam);
     void** phi_ptrs = b->adj_ptrs;
     void** lam_ptrs = b->adj_ptrs + g.ntraj;
-    GPE_CK(launch_fill_ptrs(phi_ptrs, b->adj_phi, tstride, g.ntraj, s));
-    GPE_CK(launch_fill_ptrs(lam_ptrs, lam, tstride, g.ntraj, s));
+    if (!tma && g.ndim >= 2) {
+        GPE_CK(launch_fill_ptrs(phi_ptrs, b->adj_phi, tstride, g.ntraj, s));
+        GPE_CK(launch_fill_ptrs(lam_ptrs, lam, tstride, g.ntraj, s));
+        g_launches += 2;
+    }
+    auto strided = [&](bool on_lam) -> cudaError_t {
+        for (int ax = 1; ax < g.ndim; ++ax) {
+            cudaError_t e = tma ? col_pass<T>(b, on_lam ? vlam : vphi, ax, true, s)
+                                : launch_colpass_mode<T>(g.n[ax], on_lam ? 2 : 0,
+                                                         adj_col_args<T>(b, g, ax, on_lam ? lam_ptrs : phi_ptrs, 3, true), s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     const double t_mid = ((double)step + 0.5) * b->p.dt;
     const double q = q_at_host(b, t_mid);
-    g_launches += 4 + 4 * (g.ndim - 1) + 1;
+    g_launches += 3 * (g.ndim - 1) + 3;
     // phi = K(dt/2) psi_n
-    for (int ax = 1; ax < g.ndim; ++ax)
-        GPE_CK(launch_colpass_mode<T>(g.n[ax], 0, adj_col_args<T>(b, g, ax, phi_ptrs, 3, true), s));
+    GPE_CK(strided(false));
     const AdjArgs<T> xa = adj_x_args<T>(b, g, q);
     GPE_CK(launch_xkin<T>(g.n[0], xa, reinterpret_cast<cplx<T>*>(b->adj_phi), false, s));
     // lam <- K(-dt/2) L^T K(-dt/2) lam
-    for (int ax = 1; ax < g.ndim; ++ax)
-        GPE_CK(launch_colpass_mode<T>(g.n[ax], 2, adj_col_args<T>(b, g, ax, lam_ptrs, 3, true), s));
+    GPE_CK(strided(true));
     int nparts = 0;
     GPE_CK(launch_xadj<T>(g.n[0], xa, reinterpret_cast<cplx<T>*>(lam), reinterpret_cast<const cplx<T>*>(b->adj_phi),
                           b->adj_part, &nparts, s));
     GPE_CK(launch_dq_final(b->adj_part, nparts, t_mid, b->p.n_knots, b->p.t_end, dLdq, s));
-    for (int ax = 1; ax < g.ndim; ++ax)
-        GPE_CK(launch_colpass_mode<T>(g.n[ax], 2, adj_col_args<T>(b, g, ax, lam_ptrs, 3, true), s));
+    GPE_CK(strided(true));
     return GPE_OK;
 }
 
