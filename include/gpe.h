@@ -293,14 +293,16 @@ gpe_status gpe_adjoint_step(gpe_batch* batch, const void* psi_step_in, void* lam
                             double* dLdq, void* stream);
 
 /* One checkpoint segment of the reverse sweep (Sec. 2.2 scheme; no counterpart in the
- * paper): recomputes psi_{n0} .. psi_{n0+nseg-1} from psi_ckpt = psi_{n0} (contiguous
- * [ntraj][3][sites], not modified) into ``states`` (caller-owned device workspace of nseg
- * such fields, back to back, 16-byte aligned), stepping the batch's own fields (which hold
- * psi_{n0+nseg-1} on return, with the step counter at n0 + nseg - 1), then applies
- * gpe_adjoint_step for steps n0 + nseg - 1 down to n0: lam = dL/dpsi_{n0+nseg} on entry,
- * dL/dpsi_{n0} on return, dL/dq added to dLdq.  The same kernels in the same order as
- * those calls made one by one, issued from the library without a host round trip per
- * step.  Errors: GPE_EINVAL (NULL or misaligned pointer, n0 < 0, nseg < 1),
+ * paper): from psi_ckpt = psi_{n0} (contiguous [ntraj][3][sites], not modified) it
+ * recomputes the states the reverse steps need into ``states`` (caller-owned device
+ * workspace of nseg such fields, back to back, 16-byte aligned), using the batch's own
+ * fields as scratch (their contents on return are unspecified; the step counter is
+ * n0 + nseg - 1), then pulls lam back over steps n0 + nseg - 1 down to n0: lam =
+ * dL/dpsi_{n0+nseg} on entry, dL/dpsi_{n0} on return, dL/dq added to dLdq, as
+ * gpe_adjoint_step would.  2D/3D batches recompute with merged kinetic half steps and keep
+ * K(dt/2) psi_n, the state each reverse step starts from, so the segment needs two field
+ * passes fewer per step than those calls (the results agree to rounding); 1D batches make
+ * exactly those calls.  Errors: GPE_EINVAL (NULL or misaligned pointer, n0 < 0, nseg < 1),
  * GPE_EUNSUPPORTED (as gpe_adjoint_step). */
 gpe_status gpe_adjoint_segment(gpe_batch* batch, const void* psi_ckpt, void* states, int64_t n0, int64_t nseg,
                                void* lam, double* dLdq, void* stream);

@@ -1094,48 +1094,108 @@ AdjArgs<T> adj_x_args(const gpe_batch* b, const Group& g, double q) {
     return a;
 }
 
+// Reverse step n given phi = K(dt/2) psi_n (a contiguous [ntraj][3][sites] buffer):
+//   lam <- K(-dt/2) L_n^T(phi) K(-dt/2) lam,  dL/dq_n added to dLdq.
+// The strided passes run as the tensor-map pass over a contiguous view of lam (the conjugate
+// pass as the kinetic pass with conjugated tables), else with pointer tables.
 template <typename T>
-gpe_status adjoint_step_t(gpe_batch* b, const void* psi_in, void* lam, int64_t step, double* dLdq, cudaStream_t s) {
-    gpe_status st = adj_workspace<T>(b);
-    if (st != GPE_OK) return st;
+gpe_status adjoint_from_phi(gpe_batch* b, const void* phi, void* lam, int64_t step, double* dLdq, cudaStream_t s) {
     const Group& g = b->groups[0];
-    const size_t vb = sizeof(cplx<T>);
-    const int64_t tstride = (int64_t)vb * 3 * g.sites;
-    GPE_CK(cudaMemcpyAsync(b->adj_phi, psi_in, tstride * g.ntraj, cudaMemcpyDeviceToDevice, s));
-    // strided passes: the tensor-map pass over contiguous views of phi and lam (the
-    // conjugate pass as the kinetic pass with conjugated tables), else pointer tables
-    Group vphi, vlam;
-    const bool tma = g.ndim >= 2 && adj_view<T>(b, g, b->adj_phi, false, vphi) && adj_view<T>(b, g, lam, true, vlam);
-    void** phi_ptrs = b->adj_ptrs;
+    const int64_t tstride = (int64_t)sizeof(cplx<T>) * 3 * g.sites;
+    Group vlam;
+    const bool tma = g.ndim >= 2 && adj_view<T>(b, g, lam, true, vlam);
     void** lam_ptrs = b->adj_ptrs + g.ntraj;
     if (!tma && g.ndim >= 2) {
-        GPE_CK(launch_fill_ptrs(phi_ptrs, b->adj_phi, tstride, g.ntraj, s));
         GPE_CK(launch_fill_ptrs(lam_ptrs, lam, tstride, g.ntraj, s));
-        g_launches += 2;
+        g_launches += 1;
     }
-    auto strided = [&](bool on_lam) -> cudaError_t {
+    auto strided = [&]() -> cudaError_t {
         for (int ax = 1; ax < g.ndim; ++ax) {
-            cudaError_t e = tma ? col_pass<T>(b, on_lam ? vlam : vphi, ax, true, s)
-                                : launch_colpass_mode<T>(g.n[ax], on_lam ? 2 : 0,
-                                                         adj_col_args<T>(b, g, ax, on_lam ? lam_ptrs : phi_ptrs, 3, true), s);
+            cudaError_t e = tma ? col_pass<T>(b, vlam, ax, true, s)
+                                : launch_colpass_mode<T>(g.n[ax], 2, adj_col_args<T>(b, g, ax, lam_ptrs, 3, true), s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     };
     const double t_mid = ((double)step + 0.5) * b->p.dt;
-    const double q = q_at_host(b, t_mid);
-    g_launches += 3 * (g.ndim - 1) + 3;
-    // phi = K(dt/2) psi_n
-    GPE_CK(strided(false));
-    const AdjArgs<T> xa = adj_x_args<T>(b, g, q);
-    GPE_CK(launch_xkin<T>(g.n[0], xa, reinterpret_cast<cplx<T>*>(b->adj_phi), false, s));
-    // lam <- K(-dt/2) L^T K(-dt/2) lam
-    GPE_CK(strided(true));
+    const AdjArgs<T> xa = adj_x_args<T>(b, g, q_at_host(b, t_mid));
+    g_launches += 2 * (g.ndim - 1) + 2;
+    GPE_CK(strided());
     int nparts = 0;
-    GPE_CK(launch_xadj<T>(g.n[0], xa, reinterpret_cast<cplx<T>*>(lam), reinterpret_cast<const cplx<T>*>(b->adj_phi),
+    GPE_CK(launch_xadj<T>(g.n[0], xa, reinterpret_cast<cplx<T>*>(lam), reinterpret_cast<const cplx<T>*>(phi),
                           b->adj_part, &nparts, s));
     GPE_CK(launch_dq_final(b->adj_part, nparts, t_mid, b->p.n_knots, b->p.t_end, dLdq, s));
-    GPE_CK(strided(true));
+    GPE_CK(strided());
+    return GPE_OK;
+}
+
+// phi <- K(dt/2) phi in place for a contiguous buffer (strided axes, then x).
+template <typename T>
+gpe_status half_kick(gpe_batch* b, void* phi, double q, cudaStream_t s) {
+    const Group& g = b->groups[0];
+    const int64_t tstride = (int64_t)sizeof(cplx<T>) * 3 * g.sites;
+    Group v;
+    if (g.ndim >= 2 && adj_view<T>(b, g, phi, false, v)) {
+        for (int ax = 1; ax < g.ndim; ++ax) GPE_CK(col_pass<T>(b, v, ax, true, s));
+    } else if (g.ndim >= 2) {
+        void** phi_ptrs = b->adj_ptrs;
+        GPE_CK(launch_fill_ptrs(phi_ptrs, phi, tstride, g.ntraj, s));
+        for (int ax = 1; ax < g.ndim; ++ax)
+            GPE_CK(launch_colpass_mode<T>(g.n[ax], 0, adj_col_args<T>(b, g, ax, phi_ptrs, 3, true), s));
+        g_launches += 1;
+    }
+    GPE_CK(launch_xkin<T>(g.n[0], adj_x_args<T>(b, g, q), reinterpret_cast<cplx<T>*>(phi), false, s));
+    g_launches += (g.ndim - 1) + 1;
+    return GPE_OK;
+}
+
+template <typename T>
+gpe_status adjoint_step_t(gpe_batch* b, const void* psi_in, void* lam, int64_t step, double* dLdq, cudaStream_t s) {
+    gpe_status st = adj_workspace<T>(b);
+    if (st != GPE_OK) return st;
+    const Group& g = b->groups[0];
+    const int64_t tstride = (int64_t)sizeof(cplx<T>) * 3 * g.sites;
+    GPE_CK(cudaMemcpyAsync(b->adj_phi, psi_in, tstride * g.ntraj, cudaMemcpyDeviceToDevice, s));
+    const double q = q_at_host(b, ((double)step + 0.5) * b->p.dt);
+    if ((st = half_kick<T>(b, b->adj_phi, q, s)) != GPE_OK) return st;
+    return adjoint_from_phi<T>(b, b->adj_phi, lam, step, dLdq, s);
+}
+
+// One checkpoint segment of 2D/3D batches: phi_{n0} = K(dt/2) psi_{n0} by a half kick of a
+// copy of the checkpoint, phi_{n0+1} .. phi_{n0+nseg-1} from the batch's fields stepped with
+// merged kinetic halves (after step j's strided passes the fields hold K(dt/2) psi_{n0+j+1}),
+// each copied into ``states``; then the reverse sweep from those phi.
+template <typename T>
+gpe_status adjoint_segment_t(gpe_batch* b, const void* ckpt, void* states, int64_t n0, int64_t nseg, void* lam,
+                             double* dLdq, cudaStream_t s) {
+    gpe_status st = adj_workspace<T>(b);
+    if (st != GPE_OK) return st;
+    if ((st = tune_tiles(b, s)) != GPE_OK) return st;
+    const Group& g = b->groups[0];
+    const size_t fb = sizeof(cplx<T>) * 3 * (size_t)g.sites, bb = fb * (size_t)g.ntraj;
+    const double dt = b->p.dt;
+    GPE_CK(cudaMemcpyAsync(states, ckpt, bb, cudaMemcpyDeviceToDevice, s));
+    if ((st = half_kick<T>(b, states, q_at_host(b, ((double)n0 + 0.5) * dt), s)) != GPE_OK) return st;
+    if (nseg > 1) {
+        const int ncopies = g.contiguous ? 1 : g.ntraj;
+        const size_t cb = g.contiguous ? bb : fb;
+        for (int i = 0; i < ncopies; ++i)
+            GPE_CK(cudaMemcpyAsync(g.hptrs[i], (const char*)ckpt + i * fb, cb, cudaMemcpyDeviceToDevice, s));
+        for (int ax = g.ndim - 1; ax >= 1; --ax) GPE_CK(col_pass<T>(b, g, ax, true, s));
+        for (int64_t j = 0; j + 1 < nseg; ++j) {
+            const double q = q_at_host(b, ((double)(n0 + j) + 0.5) * dt);
+            GPE_CK(x_pass<T>(b, g, j == 0, false, q, s));
+            for (int ax = 1; ax < g.ndim; ++ax) GPE_CK(col_pass<T>(b, g, ax, false, s));
+            char* dst = (char*)states + (size_t)(j + 1) * bb;
+            for (int i = 0; i < ncopies; ++i)
+                GPE_CK(cudaMemcpyAsync(dst + i * fb, g.hptrs[i], cb, cudaMemcpyDeviceToDevice, s));
+        }
+        g_launches += (g.ndim - 1) + (nseg - 1) * g.ndim;
+    }
+    b->step = n0 + nseg - 1;
+    for (int64_t j = nseg - 1; j >= 0; --j)
+        if ((st = adjoint_from_phi<T>(b, (const char*)states + (size_t)j * bb, lam, n0 + j, dLdq, s)) != GPE_OK)
+            return st;
     return GPE_OK;
 }
 
@@ -1211,10 +1271,15 @@ gpe_status gpe_adjoint_segment(gpe_batch* b, const void* psi_ckpt, void* states,
     if (n0 < 0 || nseg < 1) return fail(GPE_EINVAL, "need n0 >= 0 and nseg >= 1");
     cudaStream_t s = (cudaStream_t)stream;
     const Group& g = b->groups[0];
+    if (g.ndim >= 2) {
+        ProfScope ps(b, 5, s, 0);
+        return b->dtype == GPE_C64 ? adjoint_segment_t<float>(b, psi_ckpt, states, n0, nseg, lam, dLdq, s)
+                                   : adjoint_segment_t<double>(b, psi_ckpt, states, n0, nseg, lam, dLdq, s);
+    }
+    // 1D: the resident kernel steps the batch's fields one step per call, each psi_n copied
+    // out before its step, then the reverse steps from psi_n
     const size_t fb = (b->dtype == GPE_C64 ? sizeof(float2) : sizeof(double2)) * 3 * (size_t)g.sites;
     const size_t batch_bytes = fb * (size_t)g.ntraj;
-    // recompute: the batch's own fields step from psi_ckpt, each state copied out before its
-    // step (one copy for the whole batch when its fields are back to back)
     const int ncopies = g.contiguous ? 1 : g.ntraj;
     const size_t cb = g.contiguous ? batch_bytes : fb;
     for (int i = 0; i < ncopies; ++i)
@@ -1226,7 +1291,6 @@ gpe_status gpe_adjoint_segment(gpe_batch* b, const void* psi_ckpt, void* states,
             GPE_CK(cudaMemcpyAsync(dst + i * fb, g.hptrs[i], cb, cudaMemcpyDeviceToDevice, s));
         if (j + 1 < nseg && (st = gpe_step_batch(b, 1, stream)) != GPE_OK) return st;
     }
-    // reverse sweep from step n0 + nseg - 1 down to n0
     for (int64_t j = nseg - 1; j >= 0; --j) {
         st = gpe_adjoint_step(b, (const char*)states + (size_t)j * batch_bytes, lam, n0 + j, dLdq, stream);
         if (st != GPE_OK) return st;
