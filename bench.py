@@ -423,6 +423,7 @@ def run_ours(args):
         e2e["note"] = ("above the device-timed value by "
                        f"{100.0 * (e2e['value'] / value - 1.0):.2f} %: run-to-run noise of that size")
     tiles = b.tiles(0)
+    lanes, xthreads = b.lanes(0), b.xpass_threads(0)
     b.close()
 
     # plain FP64 comparator: one trajectory per launch, no graph
@@ -458,7 +459,8 @@ def run_ours(args):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": dict(workload_config(ws), column_tiles={"y": tiles[0], "autotuned": tiles[2]}),
+               "config": dict(workload_config(ws), column_tiles={"y": tiles[0], "autotuned": tiles[2]},
+                              xpass_threads=xthreads, trajectory_lanes=lanes),
                "per_step": per_step, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": launches, "fp64_plain": fp64, "status": status, "secondary": secondary}
         print(json.dumps(out), flush=True)
