@@ -820,3 +820,32 @@ def test_full_size_ragged_mix_sampled(B):
         ref = run_oracle(oracle_initial(shapes[i], 1, seed, ids=[i]), 0.02, steps, 2)
         assert rel_l2_per_comp(b.psi[i].cpu().numpy()[None].astype(np.complex128), ref) <= 1e-4
     b.close()
+
+
+def test_full_config_1d_256_fp64_spectra_every_100(B):
+    """The 1D workload at its full configuration: 256 points, FP64, one trajectory from the
+    noisy polar state, dt = 0.01, 1000 steps, occupation spectra, S_perp and diagnostics
+    every 100 steps (11 samples with t = 0), each sample against the oracle's run."""
+    wl = W.C1_1D
+    seed = W.SEED_BASE
+    b = B.GPEBatch(wl.shape, wl.ntraj, wl.dtype, wl.c0, wl.c1, wl.q, wl.dt, dx=wl.dx)
+    b.init_noise(seed, wl.mean_spinor(), wl.noise_per_mode)
+    nb, sd = b.layout()
+    nsamples = wl.steps // wl.sample_every + 1
+    acc = b.new_accumulator(nsamples)
+    b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 0)
+    for i in range(1, nsamples):
+        b.step(wl.sample_every)
+        b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, i)
+    assert b.sync_status() == B.GPE_OK
+    a = acc.cpu().numpy().reshape(nsamples, sd)
+    p = oracle_initial(wl.shape, 1, seed, npm=wl.noise_per_mode, mean=wl.mean_spinor())
+    for i in range(nsamples):
+        if i > 0:
+            p = run_oracle(p, wl.dt, wl.sample_every, 1, c0=wl.c0, c1=wl.c1, q=wl.q, dx=wl.dx)
+        spec, diag = B.unpack_slot(a[i], nb, 1)
+        rs, rd, _ = oracle_observables(p, wl.dx, 1, q=wl.q)
+        scale = np.abs(rs).max()
+        assert np.abs(spec - rs).max() <= 1e-10 * scale, i
+        np.testing.assert_allclose(diag, rd, rtol=1e-10, atol=1e-10 * np.abs(rd).max())
+    b.close()
