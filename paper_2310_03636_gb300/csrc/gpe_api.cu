@@ -351,8 +351,11 @@ gpe_status build_group_tables(gpe_batch* b, Group& g) {
         GPE_CK(cudaMemcpy(g.ph_full[a], pf.data(), bytes, cudaMemcpyHostToDevice));
         GPE_CK(cudaMemcpy(g.ph_half[a], ph.data(), bytes, cudaMemcpyHostToDevice));
         if (a == 0 && g.ndim >= 2) {
-            const std::vector<float2> cf = compact_phases(pf), ch = compact_phases(ph);
-            const std::vector<float2> t2 = pair_twiddles(stage_twiddles_host<T>(g.n[0], 8), g.n[0], 8);
+            std::vector<float2> cf = compact_phases(pf), ch = compact_phases(ph);
+            std::vector<float2> t2 = pair_twiddles(stage_twiddles_host<T>(g.n[0], 8), g.n[0], 8);
+            // whole 16-byte units: the x pass fetches these tables with bulk copies
+            for (auto* v : {&cf, &ch, &t2})
+                if (!v->empty() && (v->size() & 1)) v->push_back(make_float2(0.0f, 0.0f));
             if (!cf.empty() && !ch.empty() && !t2.empty()) {
                 const size_t cb = sizeof(float2) * cf.size(), tb = sizeof(float2) * t2.size();
                 if ((s = dev_alloc(b, &g.phc_full, cb)) != GPE_OK) return s;

@@ -106,7 +106,9 @@ __device__ __forceinline__ void kinetic_row(cplx<T>* row, cplx<T>* xbuf, const T
 // copies write them back.
 // Compact phase tables the x pass keeps in shared memory (CPH): one, two with the leading
 // half kick.
-template <int N, bool PRE> constexpr int xpass_cph_entries() { return ((PRE ? 2 : 1) * (N / 2 + 1) + 1) & ~1; }
+// Each table takes an even number of entries (whole 16-byte units, for the bulk copy).
+template <int N> constexpr int xpass_cph_half() { return (N / 2 + 1 + 1) & ~1; }
+template <int N, bool PRE> constexpr int xpass_cph_entries() { return (PRE ? 2 : 1) * xpass_cph_half<N>(); }
 
 template <typename T, int N, int R, bool PRE, int THREADS = 0, bool CPH = false>
 __global__ void __launch_bounds__(xpass_rows<N, R, THREADS>() * (N / R))
@@ -130,7 +132,15 @@ k_xpass(const PassArgs<T> a) {
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(bar, (uint32_t)(nrows * 3 * N * sizeof(V)));
+        // CPH: the (p, u) stage twiddles and the compact phase tables come with the rows, on
+        // the same barrier (bulk copies of whole 16-byte units; the host pads each table)
+        constexpr uint32_t CPH_BYTES = CPH ? (uint32_t)(((TWN + 1) & ~1) + xpass_cph_entries<N, PRE>()) * 8u : 0u;
+        mbar_expect_tx(bar, (uint32_t)(nrows * 3 * N * sizeof(V)) + CPH_BYTES);
+        if constexpr (CPH) {
+            bulk_g2s(tws, a.tw2, (uint32_t)(((TWN + 1) & ~1) * 8), bar);
+            bulk_g2s(phc, a.phc, (uint32_t)(xpass_cph_half<N>() * 8), bar);
+            if constexpr (PRE) bulk_g2s(phc + xpass_cph_half<N>(), a.phc_pre, (uint32_t)(xpass_cph_half<N>() * 8), bar);
+        }
         for (int r = 0; r < nrows; ++r) {
             const int64_t g = row0 + r;
             const int traj = (int)(g / a.rows_per_traj);
@@ -140,12 +150,7 @@ k_xpass(const PassArgs<T> a) {
                 bulk_g2s(D + (r * 3 + c) * N, src + c * a.comp_stride, N * sizeof(V), bar);
         }
     }
-    if constexpr (CPH) copy_table(tws, a.tw2, TWN);
-    else copy_table(tws, a.tw[tw_slot<R>()], TWN);
-    if constexpr (CPH) {
-        copy_table(phc, a.phc, N / 2 + 1);
-        if constexpr (PRE) copy_table(phc + (N / 2 + 1), a.phc_pre, N / 2 + 1);
-    }
+    if constexpr (!CPH) copy_table(tws, a.tw[tw_slot<R>()], TWN);
     const bool ok = __syncthreads_and(mbar_wait(bar, 0, first_wait_limit(a.wait_first)));
     if (!ok) {
         if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)GPE_ETIMEOUT);
@@ -157,7 +162,7 @@ k_xpass(const PassArgs<T> a) {
     if constexpr (PRE) {
 #pragma unroll 1
         for (int c = 0; c < 3; ++c)
-            kinetic_row<T, N, R, RPC, CPH, TWT>(Dr + c * N, Xr, tws, a.ph_pre, t, phc + (N / 2 + 1), a.ph_scale);
+            kinetic_row<T, N, R, RPC, CPH, TWT>(Dr + c * N, Xr, tws, a.ph_pre, t, phc + xpass_cph_half<N>(), a.ph_scale);
     }
     if (lrow < nrows) {
         if (a.vpot == nullptr) {
