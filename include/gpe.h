@@ -318,7 +318,9 @@ gpe_status gpe_sf_band_loss(gpe_batch* batch, const void* psi, double kmin, doub
 /* Measurement: when enabled, every launch the batch makes is bracketed by CUDA events on
  * its stream, summed per kernel class: 0 = x pass (local step fused with the x kinetic
  * pass), 1 = strided kinetic pass (y or z), 2 = resident 1D kernel, 3 = noise,
- * 4 = observables (whole pipeline of one call), 5 = adjoint step.  gpe_profile_read synchronises the
+ * 4 = observables (whole pipeline of one call), 5 = adjoint (one gpe_adjoint_step call, or
+ * one gpe_adjoint_segment call: its recompute and strided passes are also counted in classes
+ * 0 and 1, so the classes then overlap).  gpe_profile_read synchronises the
  * device, writes the summed milliseconds and launch counts of each class (arrays of 6,
  * host) since the last read, and resets them. */
 gpe_status gpe_profile_enable(gpe_batch* batch, int32_t enable);
