@@ -361,10 +361,11 @@ def run_ours(args):
                 "classes_launches": {k: v[1] for k, v in prof.items() if v[1]},
                 "effective_frac_16B_per_su": value / ws * 16.0 / (peak * 1e9)}
 
-    # end to end through the API with host buffers: every bench step copies its initial
-    # fields from pinned host memory, runs the sampling interval and reads its accumulator
-    # slot back.  Two field buffers (two batches of the same ensemble): the copy for step
-    # k + 1 runs on a copy stream while step k computes, the way a pipelined caller would.
+    # end to end through the API with host buffers: every bench step uploads its initial
+    # fields from pinned host memory (gpe_batch_upload), runs the sampling interval and reads
+    # its accumulator slot back (gpe_obs_download).  Two field buffers (two batches of the
+    # same ensemble): the upload for step k + 1 runs on a copy stream while step k computes,
+    # the way a pipelined caller would.
     host_psi = torch.empty_like(b.psi, device="cpu").pin_memory()
     host_psi.copy_(b.psi)
     host_acc = torch.empty(sd, dtype=torch.float64).pin_memory()
@@ -382,8 +383,7 @@ def run_ours(args):
     def put(k):
         i = k % 2
         cstream.wait_event(freed[i])   # the buffer's previous step has finished with it
-        with torch.cuda.stream(cstream):
-            bufs[i].psi.copy_(host_psi, non_blocking=True)
+        bufs[i].upload(host_psi, stream=cstream)
         copied[i].record(cstream)
 
     k_e2e = max(5, args.steps // 2)
@@ -402,7 +402,7 @@ def run_ours(args):
         stream.wait_event(copied[i])
         bufs[i].step(STEPS_PER_SAMPLE)
         bufs[i].observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 0)
-        host_acc.copy_(acc[:sd], non_blocking=True)
+        bufs[i].download_slot(acc, 0, host_acc, stream=stream)
         freed[i].record(stream)
         fe[k + 1].record(stream)
     f1.record(stream)
@@ -415,7 +415,8 @@ def run_ours(args):
            "h2d_bytes_per_step": int(b.psi.numel() * b.psi.element_size()),
            "d2h_bytes_per_step": int(sd * 8), "steps": k_e2e, "per_step": e2e_steps,
            "pipelined": "two field buffers; the next step's H2D copy overlaps the current step",
-           "api": "torch pinned-host copies around the device-pointer C ABI (the ABI takes device buffers)"}
+           "api": "C ABI with host buffers: gpe_batch_upload (pinned host fields -> batch), gpe_step_batch, "
+                  "observables_accumulate, gpe_obs_download (accumulator slot -> pinned host)"}
     # An end-to-end rate above the device-only one can only be run-to-run noise (the e2e
     # region does strictly more work); flag it instead of reporting it silently.
     e2e["above_device_value"] = e2e["value"] > value

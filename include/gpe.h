@@ -280,6 +280,20 @@ gpe_status gpe_batch_set_step(gpe_batch* batch, int64_t step);
 gpe_status gpe_batch_save(const gpe_batch* batch, const char* path, void* stream);
 gpe_status gpe_batch_load(gpe_batch* batch, const char* path, void* stream);
 
+/* Host transfers (no counterpart in the paper; for callers whose data live in host
+ * memory).  gpe_batch_upload copies host_psi -- every trajectory of the batch in batch order,
+ * each its [3][n2][n1][n0] field in the batch's precision, back to back -- into the
+ * trajectories' device fields; gpe_batch_download copies the fields out in the same layout.
+ * Trajectories whose fields are adjacent on the device go as one copy.  Asynchronous on
+ * ``stream`` (page-locked host memory lets the copy overlap other work).
+ * gpe_obs_download copies accumulator slot ``sample_slot`` of acc (device, slot_doubles of
+ * gpe_obs_layout per slot) to host.  Errors: GPE_EINVAL (NULL pointer, sample_slot < 0),
+ * GPE_ECUDA. */
+gpe_status gpe_batch_upload(gpe_batch* batch, const void* host_psi, void* stream);
+gpe_status gpe_batch_download(const gpe_batch* batch, void* host_psi, void* stream);
+gpe_status gpe_obs_download(const gpe_batch* batch, const double* acc, int32_t sample_slot, double* host,
+                            void* stream);
+
 /* Reverse-mode step (vector-Jacobian product of one Strang step, Sec. 2.2 scheme; the
  * paper itself has no adjoint).  With psi_step_in = psi_n, the fields at the start of
  * step n = step_index (contiguous [ntraj][3][sites] complex, caller-owned device memory,

@@ -63,6 +63,9 @@ def _load():
         "gpe_profile_read": ([vp, pd, ctypes.POINTER(i64)], ctypes.c_int),
         "gpe_adjoint_step": ([vp, vp, vp, i64, vp, vp], ctypes.c_int),
         "gpe_adjoint_segment": ([vp, vp, vp, i64, i64, vp, vp, vp], ctypes.c_int),
+        "gpe_batch_upload": ([vp, vp, vp], ctypes.c_int),
+        "gpe_batch_download": ([vp, vp, vp], ctypes.c_int),
+        "gpe_obs_download": ([vp, vp, i32, vp, vp], ctypes.c_int),
         "gpe_sf_band_loss": ([vp, vp, dbl, dbl, vp, vp, vp], ctypes.c_int),
         "gpe_launch_count": ([], i64),
         "gpe_batch_set_graph": ([vp, i32], ctypes.c_int),
@@ -391,6 +394,23 @@ class GPEBatch:
         t = ctypes.c_int32()
         _check(LIB.gpe_batch_get_xpass_threads(self.h, int(traj), ctypes.byref(t)))
         return int(t.value)
+
+    def upload(self, host, stream=None):
+        """Copy host fields (CPU tensor holding every trajectory in batch order, back to
+        back, the batch's dtype; pinned memory for an asynchronous copy) into the batch."""
+        assert not host.is_cuda and host.is_contiguous()
+        _check(LIB.gpe_batch_upload(self.h, ctypes.c_void_p(host.data_ptr()), _stream(stream)))
+
+    def download(self, host, stream=None):
+        """Copy the batch's fields into a host tensor laid out as for upload."""
+        assert not host.is_cuda and host.is_contiguous()
+        _check(LIB.gpe_batch_download(self.h, ctypes.c_void_p(host.data_ptr()), _stream(stream)))
+
+    def download_slot(self, acc, slot, host, stream=None):
+        """Copy accumulator slot ``slot`` of the device tensor acc into the host tensor host."""
+        assert acc.is_cuda and acc.dtype == torch.float64 and not host.is_cuda and host.dtype == torch.float64
+        _check(LIB.gpe_obs_download(self.h, ctypes.c_void_p(acc.data_ptr()), int(slot),
+                                    ctypes.c_void_p(host.data_ptr()), _stream(stream)))
 
     def set_lanes(self, lanes=-1):
         """Trajectory lanes per 2D/3D shape group (-1: the default, 1: off, at most 64)."""

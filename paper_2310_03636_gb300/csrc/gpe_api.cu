@@ -983,6 +983,61 @@ gpe_status gpe_obs_layout(const gpe_batch* b, int32_t* nbins, int64_t* slot_doub
     return GPE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Copies between a host buffer holding every trajectory of the batch in batch order, back to
+// back, and the trajectories' device fields; runs of trajectories whose fields are adjacent
+// on the device go as one copy.
+gpe_status batch_transfer(const gpe_batch* b, void* host, bool upload, cudaStream_t s) {
+    const size_t vb = b->dtype == GPE_C64 ? sizeof(float2) : sizeof(double2);
+    size_t off = 0;
+    for (size_t i = 0; i < b->trajs.size();) {
+        char* dev = static_cast<char*>(b->trajs[i].psi);
+        size_t bytes = 0, j = i;
+        for (; j < b->trajs.size(); ++j) {
+            const gpe_traj& t = b->trajs[j];
+            if (static_cast<char*>(t.psi) != dev + bytes) break;
+            bytes += vb * 3 * (size_t)t.n[0] * t.n[1] * t.n[2];
+        }
+        char* h = static_cast<char*>(host) + off;
+        GPE_CK(upload ? cudaMemcpyAsync(dev, h, bytes, cudaMemcpyHostToDevice, s)
+                      : cudaMemcpyAsync(h, dev, bytes, cudaMemcpyDeviceToHost, s));
+        off += bytes;
+        i = j;
+    }
+    return GPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gpe_status gpe_batch_upload(gpe_batch* b, const void* host_psi, void* stream) {
+    g_err.clear();
+    if (!b || !host_psi) return fail(GPE_EINVAL, "NULL argument");
+    return batch_transfer(b, const_cast<void*>(host_psi), true, (cudaStream_t)stream);
+}
+
+gpe_status gpe_batch_download(const gpe_batch* b, void* host_psi, void* stream) {
+    g_err.clear();
+    if (!b || !host_psi) return fail(GPE_EINVAL, "NULL argument");
+    return batch_transfer(b, host_psi, false, (cudaStream_t)stream);
+}
+
+gpe_status gpe_obs_download(const gpe_batch* b, const double* acc, int32_t sample_slot, double* host, void* stream) {
+    g_err.clear();
+    if (!b || !acc || !host || sample_slot < 0) return fail(GPE_EINVAL, "NULL argument or sample_slot < 0");
+    int32_t nb = 0;
+    int64_t sd = 0;
+    gpe_status st = gpe_obs_layout(b, &nb, &sd);
+    if (st != GPE_OK) return st;
+    GPE_CK(cudaMemcpyAsync(host, acc + (size_t)sample_slot * (size_t)sd, sizeof(double) * (size_t)sd,
+                           cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    return GPE_OK;
+}
+
 gpe_status gpe_obs_group_layout(const gpe_batch* b, int32_t traj, int32_t* nbins, int64_t* spectra_offset) {
     if (!b || !nbins || !spectra_offset || traj < 0 || traj >= (int32_t)b->trajs.size())
         return fail(GPE_EINVAL, "bad batch, trajectory or NULL argument");

@@ -849,3 +849,40 @@ def test_full_config_1d_256_fp64_spectra_every_100(B):
         assert np.abs(spec - rs).max() <= 1e-10 * scale, i
         np.testing.assert_allclose(diag, rd, rtol=1e-10, atol=1e-10 * np.abs(rd).max())
     b.close()
+
+
+def test_host_upload_download_round_trip(B):
+    """gpe_batch_upload / gpe_batch_download move every trajectory of the batch, in batch
+    order and back to back, between host memory and the device fields (a uniform batch: one
+    copy; a ragged one whose shape groups sit in separate allocations: several), and
+    gpe_obs_download returns one accumulator slot."""
+    for shapes in ([(64, 64)] * 3, [(256,), (64, 128), (256,), (64, 64, 64)]):
+        b = B.GPEBatch(shapes[0], len(shapes), "c64") if len(set(shapes)) == 1 else \
+            B.GPEBatch(list(shapes), dtype="c128")
+        tdt = torch.complex64 if b.dtype == B.GPE_C64 else torch.complex128
+        total = sum(3 * int(np.prod(s)) for s in shapes)
+        g = torch.Generator().manual_seed(7)
+        host = torch.complex(torch.randn(total, generator=g, dtype=torch.float64),
+                             torch.randn(total, generator=g, dtype=torch.float64)).to(tdt).pin_memory()
+        b.upload(host)
+        torch.cuda.synchronize()
+        dev = [b.psi[i] for i in range(len(shapes))] if b.uniform else b.psi
+        flat = torch.cat([p.reshape(-1).cpu() for p in dev])
+        assert torch.equal(flat, host)
+        back = torch.zeros_like(host).pin_memory()
+        b.download(back)
+        torch.cuda.synchronize()
+        assert torch.equal(back, host)
+        b.close()
+    b = B.GPEBatch((64, 64), 2, "c64")
+    b.init_noise(3, MEAN, 0.5)
+    nb, sd = b.layout()
+    acc = b.new_accumulator(3)
+    b.observables(acc, B.GPE_OBS_SPECTRA | B.GPE_OBS_DIAG, 2)
+    out = torch.zeros(sd, dtype=torch.float64).pin_memory()
+    b.download_slot(acc, 2, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, acc[2 * sd:3 * sd].cpu())
+    with pytest.raises(B.GPEError):
+        B._check(B.LIB.gpe_obs_download(b.h, acc.data_ptr(), -1, out.data_ptr(), None))
+    b.close()
