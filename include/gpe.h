@@ -253,9 +253,10 @@ gpe_status gpe_batch_set_tiles(gpe_batch* batch, int32_t traj, int32_t cols_y, i
 gpe_status gpe_batch_get_tiles(const gpe_batch* batch, int32_t traj, int32_t cols[2], int32_t* tuned);
 
 /* Block size of the x pass (local step fused with the x kinetic pass) for trajectory
- * traj's group.  FP32 2D/3D groups run it with 128 or 256 threads (the autotuner times
- * both on the first step and keeps the faster; every row goes through the same arithmetic,
- * so the choice changes no result bit).  set: 128 or 256 fixes it (the autotuner then
+ * traj's group.  FP32 2D/3D groups run it with 128 or 256 threads, or 192 at an x extent of
+ * 512 (the autotuner times each on the first step and keeps the fastest; every row goes
+ * through the same arithmetic, so the choice changes no result bit).  set: one of those
+ * sizes fixes it (the autotuner then
  * leaves it), 0 restores the default; drops the batch's captured graphs.  Errors:
  * GPE_EINVAL (bad batch, trajectory or size), GPE_EUNSUPPORTED (FP64 batches, 1D groups). */
 gpe_status gpe_batch_set_xpass_threads(gpe_batch* batch, int32_t traj, int32_t threads);

@@ -386,7 +386,8 @@ class GPEBatch:
         _check(LIB.gpe_batch_set_tiles(self.h, int(traj), int(cols_y), int(cols_z)))
 
     def set_xpass_threads(self, threads, traj=0):
-        """Fix the x-pass block size (128 or 256; 0 = default) of trajectory traj's group."""
+        """Fix the x-pass block size (128 or 256, or 192 at x extent 512; 0 = default) of
+        trajectory traj's group."""
         _check(LIB.gpe_batch_set_xpass_threads(self.h, int(traj), int(threads)))
 
     def xpass_threads(self, traj=0):

@@ -544,7 +544,9 @@ void drop_graphs(gpe_batch* b) {
 }
 
 // Block size of the x pass that the library uses for group g when none is fixed.
-int xpass_default_threads(const Group& g) { return (g.n[0] == 128 || g.n[0] == 1024) ? 128 : 256; }
+int xpass_default_threads(const Group& g) {
+    return (g.n[0] == 128 || g.n[0] == 1024) ? 128 : (g.n[0] == 512 ? 192 : 256);
+}
 
 // Times the x pass (no leading half kick) on nt scratch fields for each block size it is
 // built for and returns the fastest (0 if nothing could be timed).

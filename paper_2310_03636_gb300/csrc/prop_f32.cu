@@ -14,9 +14,11 @@ cudaError_t launch_xpass<float>(int n, bool pre, const PassArgs<float>& a, cudaS
 }
 
 template <>
-int xpass_thread_candidates<float>(int, int* threads) {
+int xpass_thread_candidates<float>(int n, int* threads) {
     for (int i = 0; i < 2; ++i) threads[i] = kXpassThreads[i];
-    return 2;
+    if (n != 512) return 2;
+    threads[2] = 192;   // three rows per block, built at 512 points only
+    return 3;
 }
 
 template <>

@@ -646,20 +646,21 @@ def test_autotuned_tiles_change_no_bit(B, shape, ntraj):
         cy, cz, tuned = b.tiles(0)
         assert tuned == tune
         assert cy in (2, 4, 8, 16) and (cz in (2, 4, 8, 16) if len(shape) == 3 else cz == 0)
-        assert b.xpass_threads(0) in (128, 256)
+        assert b.xpass_threads(0) in (128, 192, 256)
         out.append(b.psi.cpu().numpy())
         b.close()
     np.testing.assert_array_equal(out[0], out[1])
 
 
 @pytest.mark.parametrize("shape,ntraj", [((64, 64), 3), ((128, 128), 2), ((256, 64, 128), 2), ((1024, 512), 1),
-                                         ((512, 1024), 1)])
+                                         ((512, 1024), 1), ((64, 512), 5), ((64, 64, 512), 1)])
 def test_every_xpass_block_size_gives_the_same_bits(B, shape, ntraj):
-    """Both x-pass block sizes (fixed through gpe_batch_set_xpass_threads; rows per block
-    change, the per-row arithmetic does not) give the same fields bit for bit; sizes that are
-    not built and FP64 batches are refused."""
+    """Every x-pass block size (128 and 256 threads, and 192 at an x extent of 512; fixed
+    through gpe_batch_set_xpass_threads; rows per block change, the per-row arithmetic does
+    not) gives the same fields bit for bit; sizes that are not built and FP64 batches are
+    refused."""
     out = []
-    for th in (128, 256):
+    for th in ((128, 192, 256) if shape[-1] == 512 else (128, 256)):
         b = B.GPEBatch(shape, ntraj, "c64", C0, C1, Q, 0.02)
         b.set_autotune(False)
         b.set_xpass_threads(th)
@@ -669,9 +670,13 @@ def test_every_xpass_block_size_gives_the_same_bits(B, shape, ntraj):
         assert b.sync_status() == B.GPE_OK
         out.append(b.psi.cpu().numpy())
         with pytest.raises(B.GPEError):
-            b.set_xpass_threads(192)
+            b.set_xpass_threads(160)
+        if shape[-1] != 512:
+            with pytest.raises(B.GPEError):
+                b.set_xpass_threads(192)
         b.close()
-    np.testing.assert_array_equal(out[0], out[1])
+    for o in out[1:]:
+        np.testing.assert_array_equal(o, out[0])
     b = B.GPEBatch(shape, 1, "c128")
     with pytest.raises(B.GPEError) as ei:
         b.set_xpass_threads(128)
